@@ -1,0 +1,434 @@
+"""Plain CPU oracle for matrix permanents — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The
+product (``paper_2602_10141_b300``) never imports it, and it imports nothing
+from the product: the two share no code.  The one module both sides use is
+``workloads`` (seeded input generators, none of the method's arithmetic).
+
+What it computes, and where the paper defines it:
+
+* ``perm_*`` — the permanent ``perm(A) = sum_sigma prod_i a_{i,sigma(i)}``
+  (paper §1, definition) by brute force, by a row-expansion DP of the same
+  sum, and by Ryser's inclusion–exclusion formula
+  ``(-1)^n sum_S (-1)^|S| prod_i sum_{j in S} a_ij`` (paper §1, cited; §2.2)
+  with row sums recomputed from scratch — all in ``oracle.c``.
+* F_p versions with ``uint64`` and ``%`` (paper §2.1).
+* Field set-up for the Schur matrix (paper §2.1): primes ``p = 1 (mod n)``
+  below ``2**31`` by trial division, a primitive n-th root of unity ``g``,
+  and the residue matrix ``(g^{jk} mod p)``.
+* Chinese remaindering to the symmetric range (paper §2.1) in Python ints,
+  with the prime count driven by ``|perm(S_n)| <= n^{n/2}`` (paper §2.1).
+* The exact integer ``perm(S_n)`` from the counts
+  ``c_m = #{sigma : sum_i i*sigma(i) = m (mod n)}`` reduced modulo the
+  cyclotomic polynomial ``Phi_n`` (definition of ``S_n``, paper §1).
+
+Pins (tests/test_oracle_*.py) tie each function to something other than
+itself: brute force, closed forms, invariants and the paper's printed
+midpoint table (Table "midpoint", §4.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import math
+import os
+import subprocess
+from typing import Iterable, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-Wall", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i = ctypes.c_int
+        for name in ("oracle_perm_brute_r", "oracle_perm_brute_c", "oracle_perm_dp_r", "oracle_perm_dp_c"):
+            getattr(lib, name).argtypes = [i, dp, dp]
+            getattr(lib, name).restype = i
+        for name in ("oracle_perm_ryser_r", "oracle_perm_ryser_c"):
+            getattr(lib, name).argtypes = [i, dp, dp, dp]
+            getattr(lib, name).restype = i
+        for name in ("oracle_perm_brute_modp", "oracle_perm_dp_modp", "oracle_perm_ryser_modp"):
+            getattr(lib, name).argtypes = [i, u32p, ctypes.c_uint32, u32p]
+            getattr(lib, name).restype = i
+        lib.oracle_perm_ryser_modp_gray_range.argtypes = [i, u32p, ctypes.c_uint32, ctypes.c_uint64,
+                                                          ctypes.c_uint64, u32p]
+        lib.oracle_perm_ryser_modp_gray_range.restype = i
+        lib.oracle_schur_counts.argtypes = [i, u64p]
+        lib.oracle_schur_counts.restype = i
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = i
+        _lib = lib
+    return _lib
+
+
+class use_library:
+    """Context manager that makes every oracle function call a different build
+    of ``oracle.c`` (used by the planted-mistake tests)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self._saved = _lib
+        lib = ctypes.CDLL(self.path)
+        for name in dir(self._saved):
+            if name.startswith("oracle_"):
+                src, dst = getattr(self._saved, name), getattr(lib, name)
+                dst.argtypes, dst.restype = src.argtypes, src.restype
+        _lib = lib
+        return lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(_load().oracle_num_threads())
+
+
+def _real(A) -> tuple[np.ndarray, int]:
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    return A, A.shape[0]
+
+
+def _cplx(A) -> tuple[np.ndarray, int]:
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    return A.view(np.float64), A.shape[0]
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"{what} failed with code {rc}")
+
+
+# ----------------------------------------------------------------------------
+# real / complex permanents
+# ----------------------------------------------------------------------------
+
+def perm_brute(A, pair: bool = False):
+    """Definition by brute force over all n! permutations (n <= 11), long double."""
+    A = np.asarray(A)
+    out = np.zeros(4)
+    if np.iscomplexobj(A):
+        a, n = _cplx(A)
+        _check(_load().oracle_perm_brute_c(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double)), "brute_c")
+        v = complex(out[0] + out[1], out[2] + out[3])
+        return ((out[0], out[1]), (out[2], out[3])) if pair else v
+    a, n = _real(A)
+    _check(_load().oracle_perm_brute_r(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double)), "brute_r")
+    return (out[0], out[1]) if pair else float(out[0] + out[1])
+
+
+def perm_dp(A, pair: bool = False):
+    """Definition organised as a row-expansion DP over column sets, double-double.
+
+    Real n <= 26, complex n <= 25 (memory 2^n double-double values).
+    """
+    A = np.asarray(A)
+    out = np.zeros(4)
+    if np.iscomplexobj(A):
+        a, n = _cplx(A)
+        _check(_load().oracle_perm_dp_c(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double)), "dp_c")
+        return ((out[0], out[1]), (out[2], out[3])) if pair else complex(out[0] + out[1], out[2] + out[3])
+    a, n = _real(A)
+    _check(_load().oracle_perm_dp_r(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double)), "dp_r")
+    return (out[0], out[1]) if pair else float(out[0] + out[1])
+
+
+def perm_ryser(A, with_abs: bool = False):
+    """Ryser's formula by direct subset enumeration, double-double (n <= 30).
+
+    With ``with_abs`` also returns ``sum_S |prod_i r_i(S)|``: the total size
+    of the terms that cancel, which scales floating-point error bounds.
+    """
+    A = np.asarray(A)
+    out = np.zeros(4)
+    ab = np.zeros(1)
+    if np.iscomplexobj(A):
+        a, n = _cplx(A)
+        _check(_load().oracle_perm_ryser_c(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double),
+                                           _ptr(ab, ctypes.c_double)), "ryser_c")
+        v = complex(out[0] + out[1], out[2] + out[3])
+    else:
+        a, n = _real(A)
+        _check(_load().oracle_perm_ryser_r(n, _ptr(a, ctypes.c_double), _ptr(out, ctypes.c_double),
+                                           _ptr(ab, ctypes.c_double)), "ryser_r")
+        v = float(out[0] + out[1])
+    return (v, float(ab[0])) if with_abs else v
+
+
+def perm_python(A):
+    """Definition in pure Python (itertools.permutations), for tiny n only."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    if n > 8:
+        raise ValueError("pure-Python brute force is for n <= 8")
+    total = 0
+    for sigma in itertools.permutations(range(n)):
+        t = 1
+        for i in range(n):
+            t = t * A[i, sigma[i]].item()
+        total += t
+    return total
+
+
+# ----------------------------------------------------------------------------
+# F_p
+# ----------------------------------------------------------------------------
+
+def _u32(A, p) -> tuple[np.ndarray, int]:
+    A = np.asarray(A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("square matrix expected")
+    if A.size and (int(A.min()) < 0 or int(A.max()) >= p):
+        raise ValueError("entries must lie in [0, p)")
+    return np.ascontiguousarray(A.astype(np.uint32)), A.shape[0]
+
+
+def perm_modp_brute(A, p: int) -> int:
+    """perm(A) mod p by brute force (n <= 11)."""
+    a, n = _u32(A, p)
+    out = np.zeros(1, np.uint32)
+    _check(_load().oracle_perm_brute_modp(n, _ptr(a, ctypes.c_uint32), p, _ptr(out, ctypes.c_uint32)), "brute_modp")
+    return int(out[0])
+
+
+def perm_modp_dp(A, p: int) -> int:
+    """perm(A) mod p by the row-expansion DP (n <= 28)."""
+    a, n = _u32(A, p)
+    out = np.zeros(1, np.uint32)
+    _check(_load().oracle_perm_dp_modp(n, _ptr(a, ctypes.c_uint32), p, _ptr(out, ctypes.c_uint32)), "dp_modp")
+    return int(out[0])
+
+
+def perm_modp(A, p: int) -> int:
+    """perm(A) mod p by Ryser's formula, subsets in binary order (n <= 48)."""
+    a, n = _u32(A, p)
+    out = np.zeros(1, np.uint32)
+    _check(_load().oracle_perm_ryser_modp(n, _ptr(a, ctypes.c_uint32), p, _ptr(out, ctypes.c_uint32)), "ryser_modp")
+    return int(out[0])
+
+
+def ryser_modp_gray_range(A, p: int, k0: int, k1: int) -> int:
+    """sum_{k0<=k<k1} (-1)^{|g(k)|} prod_i sum_{j in g(k)} a_ij mod p, g(k) = k ^ (k >> 1).
+
+    No ``(-1)^n`` factor: over the whole range [0, 2^n) this equals
+    ``(-1)^n perm(A) mod p``.
+    """
+    a, n = _u32(A, p)
+    out = np.zeros(1, np.uint32)
+    _check(_load().oracle_perm_ryser_modp_gray_range(n, _ptr(a, ctypes.c_uint32), p, k0, k1,
+                                                     _ptr(out, ctypes.c_uint32)), "gray_range")
+    return int(out[0])
+
+
+# ----------------------------------------------------------------------------
+# Field set-up for the Schur matrix (paper §2.1)
+# ----------------------------------------------------------------------------
+
+def is_prime(m: int) -> bool:
+    """Trial division by every integer up to sqrt(m)."""
+    if m < 2:
+        return False
+    if m % 2 == 0:
+        return m == 2
+    d = 3
+    while d * d <= m:
+        if m % d == 0:
+            return False
+        d += 2
+    return True
+
+
+def primes_1_mod_n(n: int, count: int, below: int = 2 ** 31, skip: int = 0) -> list[int]:
+    """The largest primes p < ``below`` with p = 1 (mod n), in descending order.
+
+    ``skip`` drops that many of the largest ones first (to build a second,
+    disjoint prime set).
+    """
+    out = []
+    k = (below - 2) // n
+    while len(out) < count + skip and k > 0:
+        p = k * n + 1
+        if p < below and is_prime(p):
+            out.append(p)
+        k -= 1
+    return out[skip:]
+
+
+def prime_count_for(n: int) -> int:
+    """⌈((n/2)·log2 n + 2)/30⌉ + 1 primes below 2^31 (the configured count).
+
+    ``crt_modulus_suffices`` checks the exact requirement separately.
+    """
+    return math.ceil(((n / 2) * math.log2(n) + 2) / 30) + 1
+
+
+def _prime_factors(m: int) -> list[int]:
+    fs, d = [], 2
+    while d * d <= m:
+        if m % d == 0:
+            fs.append(d)
+            while m % d == 0:
+                m //= d
+        d += 1
+    if m > 1:
+        fs.append(m)
+    return fs
+
+
+def primitive_nth_root(p: int, n: int) -> int:
+    """Smallest-h choice: g = h^((p-1)/n) mod p for the smallest h >= 2 whose g
+    has multiplicative order exactly n (g^n = 1 and g^(n/q) != 1 for every
+    prime q | n)."""
+    if (p - 1) % n:
+        raise ValueError("p != 1 (mod n)")
+    qs = _prime_factors(n)
+    for h in range(2, p):
+        g = pow(h, (p - 1) // n, p)
+        if pow(g, n, p) != 1:
+            continue
+        if all(pow(g, n // q, p) != 1 for q in qs):
+            return g
+    raise ValueError("no primitive root found")
+
+
+def schur_residue_matrix(n: int, p: int, g: int) -> np.ndarray:
+    """(g^{jk} mod p)_{j,k=0..n-1} as uint32 (paper §2.1)."""
+    M = np.zeros((n, n), dtype=np.uint32)
+    for j in range(n):
+        for k in range(n):
+            M[j, k] = pow(g, j * k, p)
+    return M
+
+
+def schur_complex_matrix(n: int) -> np.ndarray:
+    """S_n = (exp(2 pi i jk / n)) (paper §1)."""
+    j = np.arange(n)
+    return np.exp(2j * np.pi * np.outer(j, j) / n)
+
+
+# ----------------------------------------------------------------------------
+# Chinese remaindering (paper §2.1)
+# ----------------------------------------------------------------------------
+
+def crt(residues: Sequence[int], primes: Sequence[int]) -> int:
+    """The unique x in (-M/2, M/2] with x = r_k (mod p_k), M = prod p_k.
+
+    Textbook construction x = sum_k r_k * M_k * (M_k^{-1} mod p_k) mod M.
+    """
+    if len(residues) != len(primes) or not primes:
+        raise ValueError("one residue per prime")
+    M = 1
+    for p in primes:
+        M *= p
+    x = 0
+    for r, p in zip(residues, primes):
+        Mk = M // p
+        x += r * Mk * pow(Mk, -1, p)
+    x %= M
+    if x > M // 2:
+        x -= M
+    return x
+
+
+def crt_modulus_suffices(n: int, primes: Iterable[int]) -> bool:
+    """True iff M = prod p > 2 * n^{n/2}, so (-M/2, M/2] holds every
+    integer of absolute value <= n^{n/2} (the bound of paper §2.1).
+    Compared exactly: M^2 > 4 n^n."""
+    M = 1
+    for p in primes:
+        M *= p
+    return M * M > 4 * n ** n
+
+
+# ----------------------------------------------------------------------------
+# Exact perm(S_n) from the permutation counts
+# ----------------------------------------------------------------------------
+
+def schur_counts(n: int) -> list[int]:
+    """c_m = #{sigma in S_n : sum_i i*sigma(i) = m (mod n)}, m = 0..n-1 (n <= 20)."""
+    out = np.zeros(n, dtype=np.uint64)
+    _check(_load().oracle_schur_counts(n, _ptr(out, ctypes.c_uint64)), "schur_counts")
+    return [int(v) for v in out]
+
+
+def _poly_divmod(num: list[int], den: list[int]) -> tuple[list[int], list[int]]:
+    """Integer polynomial long division by a monic ``den``; coefficients low to high."""
+    num = list(num)
+    dn = len(den) - 1
+    if den[-1] != 1:
+        raise ValueError("monic divisor expected")
+    q = [0] * max(len(num) - dn, 1)
+    for k in range(len(num) - 1, dn - 1, -1):
+        c = num[k]
+        if c:
+            q[k - dn] = c
+            for i in range(dn + 1):
+                num[k - dn + i] -= c * den[i]
+    rem = num[:dn] if dn > 0 else [0]
+    return q, rem
+
+
+def cyclotomic(n: int) -> list[int]:
+    """Phi_n with integer coefficients (low to high), from x^n - 1 = prod_{d | n} Phi_d."""
+    num = [-1] + [0] * (n - 1) + [1]
+    for d in range(1, n):
+        if n % d == 0:
+            num, rem = _poly_divmod(num, cyclotomic(d))
+            if any(rem):
+                raise ArithmeticError("non-exact cyclotomic division")
+    return num
+
+
+def schur_exact(n: int) -> int:
+    """perm(S_n) as an exact integer: sum_m c_m x^m reduced modulo Phi_n(x).
+
+    The remainder must be a constant (perm(S_n) is a rational integer); a
+    non-constant remainder raises.
+    """
+    c = schur_counts(n)
+    _, rem = _poly_divmod(c, cyclotomic(n))
+    if any(rem[1:]):
+        raise ArithmeticError("perm(S_n) did not reduce to an integer")
+    return rem[0]
+
+
+def schur_modp_from_counts(n: int, p: int, g: int) -> int:
+    """perm((g^{jk}) mod p) = sum_m c_m g^m mod p."""
+    return sum(c * pow(g, m, p) for m, c in enumerate(schur_counts(n))) % p
