@@ -1,0 +1,216 @@
+/*
+ * permx — Gray-code Ryser permanents on one NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper §1 for the definition and Ryser's O(n 2^n) formula;
+ * §2.2 for the Gray-code block evaluation):
+ *
+ *     perm(A) = sum_{sigma in S_n} prod_i a_{i,sigma(i)}
+ *             = (-1)^n  sum_{S subset {0..n-1}} (-1)^{|S|} prod_i sum_{j in S} a_ij .
+ *
+ * The 2^n subsets are walked in reflected-binary Gray order S_k = k ^ (k>>1):
+ * consecutive subsets differ in one column j = ctz(k), so every row sum
+ * changes by +-a_ij per step.  Over F_p (paper §2.1) the same sum is taken
+ * with residues; for the Schur matrix S_n = (w^{jk}) it is evaluated as the
+ * residue matrix (g^{jk} mod p), g a primitive n-th root of unity mod a
+ * prime p = 1 (mod n), and the exact integer is recovered by Chinese
+ * remaindering over enough primes that prod p > 2 n^{n/2} (|perm(S_n)| <=
+ * n^{n/2}, paper §2.1).
+ *
+ * Conventions for every entry point:
+ *  - Return PERMX_OK (0) on success, a negative PERMX_E* code otherwise;
+ *    perm_last_error() gives a message for the calling thread's last error.
+ *  - Matrices are square, row-major, element (i,j) at A[offset + i*n + j];
+ *    complex entries interleave (re, im).
+ *  - "device" pointers are CUDA device memory owned by the caller; the library
+ *    never frees them.  Host arrays are read before the call returns.
+ *  - Asynchronous calls enqueue work on the caller's stream (a cudaStream_t
+ *    passed as void*, NULL = the legacy default stream) and return; results
+ *    are valid once that stream has been synchronised.  Temporary device
+ *    memory is allocated stream-ordered and released on the same stream.
+ *  - The library uses whichever CUDA device is current on the calling thread.
+ *  - Limits: 1 <= n <= PERMX_MAX_N_FP for float64/complex128 and
+ *    1 <= n <= PERMX_MAX_N_MODP for F_p; primes satisfy 2 < p < 2^31.
+ */
+#ifndef PERMX_H
+#define PERMX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PERMX_OK 0
+#define PERMX_EINVAL (-1)   /* bad argument: n out of range, NULL pointer, p not an odd prime < 2^31, ... */
+#define PERMX_ENOMEM (-2)   /* device or host allocation failed */
+#define PERMX_EBUSY (-3)    /* serving: admission is full; retry after polling */
+#define PERMX_ECUDA (-4)    /* a CUDA runtime call failed (message has the CUDA error string) */
+#define PERMX_ETIMEOUT (-5) /* a bounded wait expired */
+#define PERMX_ENOTFOUND (-6) /* serving: unknown ticket */
+#define PERMX_EIO (-7)      /* checkpoint file could not be read/written or is corrupt */
+#define PERMX_EAGAIN (-8)   /* a long run stopped early at the caller's request; resume from the checkpoint */
+
+#define PERMX_MAX_N_FP 32
+#define PERMX_MAX_N_MODP 48
+
+typedef struct { double re, im; } perm_c128_t;
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char* perm_last_error(void);
+
+/* Library version string. */
+const char* permx_version(void);
+
+/* ------------------------------------------------------------------------
+ * Batched permanents (paper §1 definition, §2.2 Gray-code evaluation; the
+ * batches of §3.1, §4.1 and §5 are many independent matrices).
+ *
+ * A       device, row-major matrices; matrix b starts at element offset[b]
+ *         (elements, not bytes) and has n[b]*n[b] entries.
+ * n       host array [batch] of sizes.
+ * offset  host array [batch] of element offsets into A.
+ * batch   number of matrices (0 is allowed and does nothing).
+ * out     device array [batch]: out[b] = perm(A_b).
+ * stream  cudaStream_t or NULL.
+ *
+ * Matrices of different sizes may be mixed freely ("ragged").  The work for
+ * one matrix is split into Gray-code chunks whose size depends only on
+ * (n, field), and the chunk results are combined in a fixed order, so out[b]
+ * is bit-for-bit the same whatever else is in the batch.
+ * float64 / complex128: the row sums and products are IEEE float64; the
+ * alternating sum is accumulated with TwoSum compensation.
+ * Errors: PERMX_EINVAL for n[b] outside [1, PERMX_MAX_N_FP], NULL pointers or
+ * batch < 0; PERMX_ENOMEM; PERMX_ECUDA.  On error nothing is guaranteed about
+ * out.
+ * ---------------------------------------------------------------------- */
+int perm_c128(const perm_c128_t* A, const int32_t* n, const int64_t* offset, int64_t batch,
+              perm_c128_t* out, void* stream);
+int perm_f64(const double* A, const int32_t* n, const int64_t* offset, int64_t batch,
+             double* out, void* stream);
+
+/* F_p permanents (paper §2.1).  A holds residues in [0, p[b]) (entries >= p
+ * give unspecified results; the checked host path perm_modp_host rejects
+ * them), p host array [batch] of primes 2 < p < 2^31, out device array
+ * [batch] of canonical residues in [0, p[b]).  1 <= n[b] <= PERMX_MAX_N_MODP.
+ * Exact: the result does not depend on chunking or batch composition. */
+int perm_modp(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
+              int64_t batch, uint32_t* out, void* stream);
+
+/* Host-buffer variants: A and out in host memory; the call copies A to the
+ * device, runs the batched path on `stream`, copies out back and
+ * synchronises the stream before returning.  The modp variant also checks
+ * every entry against its prime (PERMX_EINVAL otherwise). */
+int perm_c128_host(const perm_c128_t* A, const int32_t* n, const int64_t* offset, int64_t batch,
+                   perm_c128_t* out, void* stream);
+int perm_f64_host(const double* A, const int32_t* n, const int64_t* offset, int64_t batch,
+                  double* out, void* stream);
+int perm_modp_host(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
+                   int64_t batch, uint32_t* out, void* stream);
+
+/* Signed Ryser partial sum of one F_p matrix over a range of Gray indices
+ * (paper §2.2: one contiguous Gray-code block):
+ *     out = sum_{k0 <= k < k1} (-1)^{|S_k|} prod_i sum_{j in S_k} a_ij  mod p,
+ * S_k = k ^ (k >> 1), without the (-1)^n factor.  A is a device n*n matrix,
+ * out a host pointer; synchronous.  k0 <= k1 <= 2^n.  Used for checkpointed
+ * long runs; summing the ranges of a partition of [0, 2^n) and multiplying
+ * by (-1)^n gives perm(A) mod p. */
+int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, uint64_t k1,
+                         uint32_t* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Exact perm(S_n) of the Schur matrix S_n = (exp(2 pi i jk/n))_{j,k<n}
+ * (paper §1; §2.1 CRT method).
+ *
+ * n          1 <= n <= PERMX_MAX_N_MODP.
+ * nprimes    number of primes; 0 = automatic: ceil(((n/2) log2 n + 2)/30) + 1,
+ *            raised if needed until prod p > 2 n^{n/2}.  A request whose
+ *            product does not exceed 2 n^{n/2} is rejected (PERMX_EINVAL).
+ *            The primes are the largest p < 2^31 with p = 1 (mod n), in
+ *            descending order; g is h^((p-1)/n) for the smallest h >= 2 of
+ *            order exactly n.  One further prime (the next one below) checks
+ *            the reconstruction: its residue must equal the CRT value mod it.
+ * ckpt_path  NULL, or a file that records finished primes and the Gray-index
+ *            cursor of the current one (written atomically after every slice:
+ *            temp file + rename).  An existing, matching file is resumed.
+ * out_i128   host [2]: the result as a two's-complement 128-bit integer
+ *            (out_i128[0] = low 64 bits, out_i128[1] = high 64 bits); PERMX_EINVAL if it does not fit.
+ * out_dec    host buffer for the decimal string (may be NULL).
+ * Synchronous.  Errors: PERMX_EINVAL, PERMX_ECUDA, PERMX_EIO, and
+ * PERMX_EAGAIN when stopped by perm_schur_crt_ex's slice limit. */
+int perm_schur_crt(int32_t n, int32_t nprimes, const char* ckpt_path, int64_t out_i128[2],
+                   char* out_dec, size_t out_dec_len);
+
+/* As perm_schur_crt, plus: slice_subsets = Gray indices per device slice
+ * between checkpoints (0 = automatic); max_slices = stop with PERMX_EAGAIN
+ * after that many slices in this call (0 = no limit); residues_out (host,
+ * may be NULL) receives the residue of every prime used, check prime last,
+ * and primes_out (host, may be NULL) the primes; both need room for
+ * nprimes+1 entries (PERMX_MAX_PRIMES is always enough). */
+#define PERMX_MAX_PRIMES 64
+int perm_schur_crt_ex(int32_t n, int32_t nprimes, const char* ckpt_path, uint64_t slice_subsets,
+                      int64_t max_slices, int64_t out_i128[2], char* out_dec, size_t out_dec_len,
+                      uint32_t* residues_out, uint32_t* primes_out);
+
+/* ------------------------------------------------------------------------
+ * Host-side field and CRT helpers (paper §2.1); no GPU needed.
+ * ---------------------------------------------------------------------- */
+/* The `count` largest primes p < 2^31 with p = 1 (mod n), descending,
+ * after skipping the first `skip` of them.  Returns count or a negative code. */
+int perm_primes_1_mod_n(int32_t n, int32_t count, int32_t skip, uint32_t* primes_out);
+/* g = h^((p-1)/n) for the smallest h >= 2 such that g has order exactly n. */
+int perm_primitive_root(uint32_t p, int32_t n, uint32_t* g_out);
+/* Residue matrix (g^{jk} mod p), row-major n*n, host memory. */
+int perm_schur_residues(int32_t n, uint32_t p, uint32_t g, uint32_t* out);
+/* Garner CRT to the symmetric range (-M/2, M/2]; PERMX_EINVAL if the value
+ * does not fit in a signed 128-bit integer or k is out of [1, PERMX_MAX_PRIMES]. */
+int perm_crt(const uint32_t* residues, const uint32_t* primes, int32_t k, int64_t out_i128[2]);
+/* Automatic prime count for perm(S_n) (see perm_schur_crt). */
+int perm_schur_prime_count(int32_t n);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of permanent requests (the batches of §3-§5
+ * arriving as a stream).  A server owns a CUDA stream, device slots for
+ * matrices and partial sums, and a host queue.  serve_submit copies the
+ * matrix and returns a ticket at once; admitted requests are advanced by
+ * bounded steps (a fixed budget of Gray-code chunks per step), new arrivals
+ * join at the next step, and a request completes when all its chunks are
+ * summed.  Each result equals the batched-path result for the same matrix.
+ * Thread-safe: submit and poll may be called from different threads.
+ * ---------------------------------------------------------------------- */
+#define PERMX_FIELD_C128 0
+#define PERMX_FIELD_F64 1
+#define PERMX_FIELD_MODP 2
+
+typedef struct {
+    int32_t max_requests;        /* queue + in-flight capacity; submit returns PERMX_EBUSY beyond it (0 = 65536) */
+    int32_t max_resident;        /* requests resident on the device at once (0 = 4096) */
+    int64_t device_bytes;        /* device memory budget for resident matrices and partials (0 = 1 GiB) */
+    int64_t chunks_per_step;     /* Gray-code chunks advanced per step (0 = automatic) */
+    int32_t device;              /* CUDA device ordinal */
+    int32_t plain_fifo;          /* 1 = baseline: one request at a time, one launch per request */
+} perm_serve_cfg;
+
+typedef struct perm_server perm_server;
+
+int serve_create(const perm_serve_cfg* cfg, perm_server** h);
+/* field: PERMX_FIELD_*; A_host: n*n entries (perm_c128_t, double or uint32_t);
+ * p: prime for MODP (ignored otherwise).  Errors: EINVAL, EBUSY. */
+int serve_submit(perm_server* h, int field, int32_t n, const void* A_host, uint32_t p, uint64_t* ticket);
+/* *done = 1 and result written (16, 8 or 4 bytes) when finished, else *done = 0.
+ * A finished ticket is released by the poll that reports it. */
+int serve_poll(perm_server* h, uint64_t ticket, void* result, int* done);
+/* As serve_poll, and on completion also the submit and completion times
+ * (nanoseconds on the host's steady clock) measured inside the library. */
+int serve_poll_timed(perm_server* h, uint64_t ticket, void* result, int* done, int64_t* t_submit_ns,
+                     int64_t* t_done_ns);
+/* Block until every submitted request is finished or timeout_ms passes (PERMX_ETIMEOUT). */
+int serve_drain(perm_server* h, int64_t timeout_ms);
+/* Counters: submitted, completed, resident, steps, launches (host array of 5). */
+int serve_stats(perm_server* h, int64_t* stats5);
+int serve_destroy(perm_server* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERMX_H */

@@ -1,0 +1,245 @@
+"""permx: Gray-code Ryser permanents on one B300 — Python binding.
+
+A thin ctypes layer over ``libpermx.so`` (the C-ABI in ``include/permx.h``):
+the functions below carry the C names and only marshal arguments.  Device
+tensors come from PyTorch (device memory and streams only); every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if the library is missing or fails to load, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpermx.so")
+
+PERMX_OK = 0
+PERMX_EINVAL = -1
+PERMX_ENOMEM = -2
+PERMX_EBUSY = -3
+PERMX_ECUDA = -4
+PERMX_ETIMEOUT = -5
+PERMX_ENOTFOUND = -6
+PERMX_EIO = -7
+PERMX_EAGAIN = -8
+MAX_N_FP = 32
+MAX_N_MODP = 48
+MAX_PRIMES = 64
+FIELD_C128, FIELD_F64, FIELD_MODP = 0, 1, 2
+
+
+class PermxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"permx error {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2602_10141_b300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    P = ctypes.POINTER
+    sig = {
+        "perm_last_error": ([], ctypes.c_char_p),
+        "permx_version": ([], ctypes.c_char_p),
+        "perm_c128": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
+        "perm_f64": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
+        "perm_modp": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
+        "perm_c128_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
+        "perm_f64_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
+        "perm_modp_host": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
+        "perm_modp_gray_range": ([vp, i32, u32, u64, u64, P(u32), vp], ctypes.c_int),
+        "perm_schur_crt": ([i32, i32, ctypes.c_char_p, P(i64), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+        "perm_schur_crt_ex": ([i32, i32, ctypes.c_char_p, u64, i64, P(i64), ctypes.c_char_p, ctypes.c_size_t,
+                               P(u32), P(u32)], ctypes.c_int),
+        "perm_primes_1_mod_n": ([i32, i32, i32, P(u32)], ctypes.c_int),
+        "perm_primitive_root": ([u32, i32, P(u32)], ctypes.c_int),
+        "perm_schur_residues": ([i32, u32, u32, P(u32)], ctypes.c_int),
+        "perm_crt": ([P(u32), P(u32), i32, P(i64)], ctypes.c_int),
+        "perm_schur_prime_count": ([i32], ctypes.c_int),
+        "permx_peak_probe": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                              P(ctypes.c_double)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def last_error() -> str:
+    return _lib.perm_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise PermxError(rc, last_error())
+    return rc
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def version() -> str:
+    return _lib.permx_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# batched device calls (arguments: device tensors + host index arrays)
+# ---------------------------------------------------------------------------
+
+def perm_c128(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
+    """out[b] = perm of the n[b] x n[b] complex128 matrix at A.view(-1)[offset[b]:]."""
+    n, offset = _i32(n), _i64(offset)
+    _check(_lib.perm_c128(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
+                          out.data_ptr(), _stream(stream)))
+    return out
+
+
+def perm_f64(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
+    n, offset = _i32(n), _i64(offset)
+    _check(_lib.perm_f64(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
+                         out.data_ptr(), _stream(stream)))
+    return out
+
+
+def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out, stream=None):
+    """A: device int32/uint32 residues (< p[b]); out: device int32 tensor of residues."""
+    n, offset, p = _i32(n), _i64(offset), _u32(p)
+    _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
+                          _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# host-buffer calls (numpy in, numpy out; copies and sync inside the library)
+# ---------------------------------------------------------------------------
+
+def perm_c128_host(A: np.ndarray, n, offset, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n, offset = _i32(n), _i64(offset)
+    out = np.empty(len(n), np.complex128) if out is None else out
+    _check(_lib.perm_c128_host(A.ctypes.data, _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
+                               out.ctypes.data, _stream(stream)))
+    return out
+
+
+def perm_f64_host(A: np.ndarray, n, offset, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n, offset = _i32(n), _i64(offset)
+    out = np.empty(len(n), np.float64) if out is None else out
+    _check(_lib.perm_f64_host(A.ctypes.data, _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
+                              out.ctypes.data, _stream(stream)))
+    return out
+
+
+def perm_modp_host(A: np.ndarray, n, offset, p, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    n, offset, p = _i32(n), _i64(offset), _u32(p)
+    out = np.empty(len(n), np.uint32) if out is None else out
+    _check(_lib.perm_modp_host(A.ctypes.data, _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
+                               _p(p, ctypes.c_uint32), len(n), out.ctypes.data, _stream(stream)))
+    return out
+
+
+def perm_modp_gray_range(A, n: int, p: int, k0: int, k1: int, stream=None) -> int:
+    """Signed Ryser sum over Gray indices [k0, k1) of one device matrix, mod p (no (-1)^n)."""
+    r = ctypes.c_uint32(0)
+    _check(_lib.perm_modp_gray_range(A.data_ptr(), n, p, k0, k1, ctypes.byref(r), _stream(stream)))
+    return int(r.value)
+
+
+# ---------------------------------------------------------------------------
+# Schur permanent and field helpers
+# ---------------------------------------------------------------------------
+
+def _i128(v: np.ndarray) -> int:
+    m = (1 << 64) - 1
+    x = ((int(v[1]) & m) << 64) | (int(v[0]) & m)
+    return x - (1 << 128) if x >> 127 else x
+
+
+def perm_schur_crt(n: int, nprimes: int = 0, ckpt_path: str | None = None) -> int:
+    """Exact perm(S_n) as a Python int (via the decimal output)."""
+    buf = ctypes.create_string_buffer(512)
+    _check(_lib.perm_schur_crt(n, nprimes, ckpt_path.encode() if ckpt_path else None, None, buf, len(buf)))
+    return int(buf.value.decode())
+
+
+def perm_schur_crt_ex(n: int, nprimes: int = 0, ckpt_path: str | None = None, slice_subsets: int = 0,
+                      max_slices: int = 0):
+    """Returns (value, primes, residues); raises PermxError with code PERMX_EAGAIN when stopped early."""
+    buf = ctypes.create_string_buffer(512)
+    res = np.zeros(MAX_PRIMES, np.uint32)
+    pr = np.zeros(MAX_PRIMES, np.uint32)
+    rc = _lib.perm_schur_crt_ex(n, nprimes, ckpt_path.encode() if ckpt_path else None, slice_subsets, max_slices,
+                                None, buf, len(buf), _p(res, ctypes.c_uint32), _p(pr, ctypes.c_uint32))
+    _check(rc)
+    k = int(np.count_nonzero(pr))
+    return int(buf.value.decode()), [int(x) for x in pr[:k]], [int(x) for x in res[:k]]
+
+
+def perm_primes_1_mod_n(n: int, count: int, skip: int = 0) -> list[int]:
+    out = np.zeros(max(count, 1), np.uint32)
+    _check(_lib.perm_primes_1_mod_n(n, count, skip, _p(out, ctypes.c_uint32)))
+    return [int(x) for x in out[:count]]
+
+
+def perm_primitive_root(p: int, n: int) -> int:
+    g = ctypes.c_uint32(0)
+    _check(_lib.perm_primitive_root(p, n, ctypes.byref(g)))
+    return int(g.value)
+
+
+def perm_schur_residues(n: int, p: int, g: int) -> np.ndarray:
+    out = np.zeros((n, n), np.uint32)
+    _check(_lib.perm_schur_residues(n, p, g, _p(out, ctypes.c_uint32)))
+    return out
+
+
+def perm_crt(residues: Sequence[int], primes: Sequence[int]) -> int:
+    r, p = _u32(residues), _u32(primes)
+    out = np.zeros(2, np.int64)
+    _check(_lib.perm_crt(_p(r, ctypes.c_uint32), _p(p, ctypes.c_uint32), len(r), _p(out, ctypes.c_int64)))
+    return _i128(out)
+
+
+def perm_schur_prime_count(n: int) -> int:
+    return _check(_lib.perm_schur_prime_count(n))
+
+
+def permx_peak_probe(kind: int, blocks: int, threads: int, iters: int) -> tuple[float, float]:
+    """(operations per second, milliseconds) of one issue-rate probe kernel."""
+    ops, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.permx_peak_probe(kind, blocks, threads, iters, ctypes.byref(ops), ctypes.byref(ms)))
+    return ops.value, ms.value

@@ -1,0 +1,426 @@
+// Batched (ragged) permanents: planning, column-major staging, launches and
+// fixed-order finalisation.  Entry points perm_modp / perm_f64 / perm_c128.
+//
+// A call groups the matrices by n (one compile-time kernel per n), stages each
+// matrix column-major into a stream-ordered workspace (column j contiguous,
+// padded to 16 bytes), launches one Ryser kernel per group and finishes with
+// one finalize kernel for the whole batch.  Per-matrix results do not depend on
+// the batch: the chunking is a function of (n, field) only and chunk partials
+// are combined in a fixed order.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "batch.h"
+#include "common.cuh"
+
+namespace permx {
+
+int chunk_log2_modp(int n) {
+    // Enough chunks to fill the GPU for one large matrix (about 2^22 chunks),
+    // at least 2^8 subsets per chunk so the O(n^2) chunk start stays < 1%.
+    int ell = n - 22;
+    int lo = n < 8 ? n : 8;
+    return ell < lo ? lo : ell;
+}
+
+int chunk_log2_fp(int n, bool cplx) {
+    // At most 2^12 steps per chunk (row-sum drift of an incremental walk grows
+    // like sqrt(L) ulps); at least 2^6 (or all of 2^n) for the chunk start cost.
+    (void)cplx;
+    int ell = n - 14;
+    int lo = n < 6 ? n : 6;
+    if (ell < lo) ell = lo;
+    if (ell > 12) ell = 12;
+    return ell;
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// ---------------------------------------------------------------------------
+// device kernels: staging and finalisation
+// ---------------------------------------------------------------------------
+
+// One block per matrix: colT[dst + j*ld + i] = A[src + i*n + j] (elements of
+// `W` 32-bit words each).
+template <typename T>
+__global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
+    const StageDesc s = d[blockIdx.x];
+    const int n = s.n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        colT[s.dst + (int64_t)j * s.ld + i] = A[s.src + e];
+    }
+    for (int e = threadIdx.x; e < n * (s.ld - n); e += blockDim.x) {   // zero the padding
+        const int j = e / (s.ld - n), i = n + e % (s.ld - n);
+        colT[s.dst + (int64_t)j * s.ld + i] = T{};
+    }
+}
+
+__device__ __forceinline__ uint32_t mulmod_u64(uint64_t a, uint64_t b, uint32_t p) {
+    return (uint32_t)((a % p) * (b % p) % p);
+}
+
+__global__ void finalize_modp_kernel(const unsigned long long* __restrict__ acc, const ModpFinal* __restrict__ f,
+                                     int64_t count, uint32_t* __restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    const ModpFinal x = f[b];
+    uint32_t v = mulmod_u64(acc[b] % x.p, x.rfix, x.p);
+    if (x.negate && v) v = x.p - v;
+    out[x.out_index] = v;
+}
+
+__device__ __forceinline__ void dd_pair_add(double& s, double& c, double s2, double c2) {
+    double t = s + s2;
+    double bp = t - s;
+    double err = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = (c + c2) + err;
+}
+
+// One block (kFinalThreads threads) per matrix; thread t folds partials
+// t, t + kFinalThreads, ... in order, then a fixed binary tree.
+constexpr int kFinalThreads = 128;
+__global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double* __restrict__ partial,
+                                                                    const FpFinal* __restrict__ f,
+                                                                    int cplx, void* __restrict__ out) {
+    __shared__ double sh[4][kFinalThreads];
+    const FpFinal x = f[blockIdx.x];
+    const int w = cplx ? 4 : 2;
+    double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+    for (int64_t q = threadIdx.x; q < x.count; q += kFinalThreads) {
+        const double* pq = partial + (x.first + q) * w;
+        dd_pair_add(s0, c0, pq[0], pq[1]);
+        if (cplx) dd_pair_add(s1, c1, pq[2], pq[3]);
+    }
+    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = c0; sh[2][threadIdx.x] = s1; sh[3][threadIdx.x] = c1;
+    __syncthreads();
+    for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            double a = sh[0][threadIdx.x], ac = sh[1][threadIdx.x];
+            dd_pair_add(a, ac, sh[0][threadIdx.x + h], sh[1][threadIdx.x + h]);
+            sh[0][threadIdx.x] = a; sh[1][threadIdx.x] = ac;
+            double b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
+            dd_pair_add(b, bc, sh[2][threadIdx.x + h], sh[3][threadIdx.x + h]);
+            sh[2][threadIdx.x] = b; sh[3][threadIdx.x] = bc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sg = x.negate ? -1.0 : 1.0;
+        const double re = sg * (sh[0][0] + sh[1][0]);
+        if (cplx) {
+            const double im = sg * (sh[2][0] + sh[3][0]);
+            reinterpret_cast<double2*>(out)[x.out_index] = make_double2(re, im);
+        } else {
+            reinterpret_cast<double*>(out)[x.out_index] = re;
+        }
+    }
+}
+
+// Server variant: accumulators and outputs at arbitrary indices.
+__global__ void finalize_modp_at_kernel(const unsigned long long* __restrict__ acc, const ModpFinalAt* __restrict__ f,
+                                        int64_t count, uint32_t* __restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    const ModpFinalAt x = f[b];
+    uint32_t v = mulmod_u64(acc[x.acc_index] % x.p, x.rfix, x.p);
+    if (x.negate && v) v = x.p - v;
+    out[x.out_index] = v;
+}
+
+cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t count, void* colT, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (field == (int)Field::MODP)
+        stage_columns_kernel<uint32_t><<<(unsigned)count, 256, 0, s>>>(static_cast<const uint32_t*>(A), d,
+                                                                         static_cast<uint32_t*>(colT));
+    else if (field == (int)Field::F64)
+        stage_columns_kernel<double><<<(unsigned)count, 256, 0, s>>>(static_cast<const double*>(A), d,
+                                                                       static_cast<double*>(colT));
+    else
+        stage_columns_kernel<double2><<<(unsigned)count, 256, 0, s>>>(static_cast<const double2*>(A), d,
+                                                                        static_cast<double2*>(colT));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
+                               cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    finalize_fp_kernel<<<(unsigned)count, kFinalThreads, 0, s>>>(partial, f, cplx ? 1 : 0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_modp_at(const unsigned long long* acc, const ModpFinalAt* f, int64_t count, uint32_t* out,
+                                    cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    finalize_modp_at_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(acc, f, count, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// primes seen before (checked once per process)
+std::mutex g_prime_mu;
+std::vector<uint32_t> g_prime_ok;
+
+bool checked_prime(uint32_t p) {
+    {
+        std::lock_guard<std::mutex> lk(g_prime_mu);
+        if (std::find(g_prime_ok.begin(), g_prime_ok.end(), p) != g_prime_ok.end()) return true;
+    }
+    if (p <= 2 || p >= (1u << 31) || !is_prime_u32(p)) return false;
+    std::lock_guard<std::mutex> lk(g_prime_mu);
+    if (g_prime_ok.size() > 4096) g_prime_ok.clear();
+    g_prime_ok.push_back(p);
+    return true;
+}
+
+}  // namespace
+
+int validate_batch(const void* A, const int32_t* n, const int64_t* offset, int64_t batch, const void* out,
+                   int max_n) {
+    if (batch < 0) return fail(PERMX_EINVAL, "batch < 0");
+    if (batch == 0) return PERMX_OK;
+    if (!A || !n || !offset || !out) return fail(PERMX_EINVAL, "NULL pointer argument");
+    for (int64_t b = 0; b < batch; ++b) {
+        if (n[b] < 1 || n[b] > max_n)
+            return fail(PERMX_EINVAL, "n[" + std::to_string(b) + "] = " + std::to_string(n[b]) + " outside [1, " +
+                                          std::to_string(max_n) + "]");
+        if (offset[b] < 0) return fail(PERMX_EINVAL, "offset[" + std::to_string(b) + "] < 0");
+    }
+    return PERMX_OK;
+}
+
+BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field) {
+    BatchPlan P;
+    P.field = field;
+    std::map<int, std::vector<int64_t>> by_n;
+    for (int64_t b = 0; b < batch; ++b) by_n[n[b]].push_back(b);
+    int64_t col_off = 0, mat_index = 0, part_off = 0;
+    for (auto& kv : by_n) {
+        GroupPlan g;
+        g.n = kv.first;
+        g.mats = std::move(kv.second);
+        g.ell = field == Field::MODP ? chunk_log2_modp(g.n) : chunk_log2_fp(g.n, field == Field::C128);
+        g.log2_chunks = g.n - g.ell;
+        if (field == Field::MODP) g.ld = pad4(g.n);
+        else if (field == Field::F64) g.ld = pad2(g.n);
+        else g.ld = g.n;                          // complex entries are 16 bytes already
+        const int words = field == Field::C128 ? 2 : 1;   // doubles (fp) or uint32 (modp) per entry
+        g.mat_stride = (int64_t)g.n * g.ld * words;
+        g.col_off = col_off;
+        g.first_mat = mat_index;
+        g.items = (int64_t)g.mats.size() << g.log2_chunks;
+        const int lg = g.log2_chunks >= 5 ? 5 : g.log2_chunks;
+        g.partials_per_mat = (int64_t)1 << (g.log2_chunks - lg);
+        g.part_off = part_off;
+        col_off += g.mat_stride * (int64_t)g.mats.size();
+        mat_index += (int64_t)g.mats.size();
+        part_off += g.partials_per_mat * (int64_t)g.mats.size();
+        P.groups.push_back(std::move(g));
+    }
+    P.col_elems = col_off;
+    P.total_partials = part_off;
+    P.batch = batch;
+    return P;
+}
+
+uint64_t plan_units(const BatchPlan& P) {
+    uint64_t u = 0;
+    for (auto& g : P.groups) u += (uint64_t)g.mats.size() * (uint64_t)g.n << g.n;
+    return u;
+}
+
+static int alloc_ws(Workspace& ws, size_t bytes, cudaStream_t s) {
+    ws.bytes = bytes;
+    if (bytes == 0) return PERMX_OK;
+    cudaError_t e = cudaMallocAsync(&ws.base, bytes, s);
+    if (e != cudaSuccess) {
+        ws.base = nullptr;
+        return e == cudaErrorMemoryAllocation ? fail(PERMX_ENOMEM, "workspace allocation failed")
+                                              : cuda_fail(e, "cudaMallocAsync");
+    }
+    return PERMX_OK;
+}
+
+int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
+                   uint32_t* out, cudaStream_t s) {
+    BatchPlan P = plan_batch(n, batch, Field::MODP);
+    // host metadata
+    std::vector<StageDesc> stage(batch);
+    std::vector<uint32_t> pp(batch), pinv(batch);
+    std::vector<ModpFinal> fin(batch);
+    for (auto& g : P.groups) {
+        for (size_t q = 0; q < g.mats.size(); ++q) {
+            const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
+            stage[m] = StageDesc{offset[b], g.col_off + (int64_t)q * g.mat_stride, g.n, g.ld};
+            pp[m] = p[b];
+            pinv[m] = inv_mod_2_32(p[b]);
+            fin[m].p = p[b];
+            fin[m].rfix = pow_mod((uint32_t)(((uint64_t)1 << 32) % p[b]), (uint64_t)(g.n - 1), p[b]);
+            fin[m].negate = g.n & 1;
+            fin[m].out_index = b;
+        }
+    }
+    const size_t o_stage = 0;
+    const size_t o_p = align256(o_stage + sizeof(StageDesc) * batch);
+    const size_t o_pinv = align256(o_p + 4 * batch);
+    const size_t o_fin = align256(o_pinv + 4 * batch);
+    const size_t o_meta_end = align256(o_fin + sizeof(ModpFinal) * batch);
+    const size_t o_acc = o_meta_end;
+    const size_t o_col = align256(o_acc + 8 * batch);
+    const size_t total = align256(o_col + 4 * (size_t)P.col_elems);
+    std::vector<unsigned char> host(o_meta_end);
+    std::memcpy(host.data() + o_stage, stage.data(), sizeof(StageDesc) * batch);
+    std::memcpy(host.data() + o_p, pp.data(), 4 * batch);
+    std::memcpy(host.data() + o_pinv, pinv.data(), 4 * batch);
+    std::memcpy(host.data() + o_fin, fin.data(), sizeof(ModpFinal) * batch);
+
+    Workspace ws;
+    int rc = alloc_ws(ws, total, s);
+    if (rc) return rc;
+    unsigned char* d = static_cast<unsigned char*>(ws.base);
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), o_meta_end, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_acc, 0, 8 * batch, s);
+    if (e == cudaSuccess) {
+        stage_columns_kernel<uint32_t><<<(unsigned)batch, 256, 0, s>>>(
+            A, reinterpret_cast<const StageDesc*>(d + o_stage), reinterpret_cast<uint32_t*>(d + o_col));
+        e = cudaGetLastError();
+    }
+    for (size_t gi = 0; e == cudaSuccess && gi < P.groups.size(); ++gi) {
+        const GroupPlan& g = P.groups[gi];
+        ModpLaunch L;
+        L.colT = reinterpret_cast<const uint32_t*>(d + o_col) + g.col_off;
+        L.p = reinterpret_cast<const uint32_t*>(d + o_p) + g.first_mat;
+        L.pinv = reinterpret_cast<const uint32_t*>(d + o_pinv) + g.first_mat;
+        L.acc = reinterpret_cast<unsigned long long*>(d + o_acc) + g.first_mat;
+        L.mat_stride = g.mat_stride;
+        L.item_begin = 0;
+        L.item_end = (uint64_t)g.items;
+        L.k_lo = 0;
+        L.k_hi = (uint64_t)1 << g.n;
+        L.ell = g.ell;
+        L.log2_chunks = g.log2_chunks;
+        e = dispatch_modp(g.n, L, s);
+    }
+    if (e == cudaSuccess) {
+        finalize_modp_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const unsigned long long*>(d + o_acc), reinterpret_cast<const ModpFinal*>(d + o_fin),
+            batch, out);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(ws.base, s);
+    if (e != cudaSuccess) return cuda_fail(e, "perm_modp launch");
+    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+    return PERMX_OK;
+}
+
+int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64_t batch, void* out, bool cplx,
+                 cudaStream_t s) {
+    BatchPlan P = plan_batch(n, batch, cplx ? Field::C128 : Field::F64);
+    const int w = cplx ? 2 : 1;   // doubles per entry
+    std::vector<StageDesc> stage(batch);
+    std::vector<FpFinal> fin(batch);
+    for (auto& g : P.groups) {
+        for (size_t q = 0; q < g.mats.size(); ++q) {
+            const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
+            // staging works on entries of w doubles: offsets in entries
+            stage[m] = StageDesc{offset[b], (g.col_off / w) + (int64_t)q * (g.mat_stride / w), g.n, g.ld};
+            fin[m].first = g.part_off + (int64_t)q * g.partials_per_mat;
+            fin[m].count = g.partials_per_mat;
+            fin[m].negate = g.n & 1;
+            fin[m].out_index = b;
+        }
+    }
+    const int pw = cplx ? 4 : 2;   // doubles per partial
+    const size_t o_stage = 0;
+    const size_t o_fin = align256(sizeof(StageDesc) * batch);
+    const size_t o_meta_end = align256(o_fin + sizeof(FpFinal) * batch);
+    const size_t o_part = o_meta_end;
+    const size_t o_col = align256(o_part + 8 * (size_t)pw * (size_t)P.total_partials);
+    const size_t total = align256(o_col + 8 * (size_t)P.col_elems);
+    std::vector<unsigned char> host(o_meta_end);
+    std::memcpy(host.data() + o_stage, stage.data(), sizeof(StageDesc) * batch);
+    std::memcpy(host.data() + o_fin, fin.data(), sizeof(FpFinal) * batch);
+
+    Workspace ws;
+    int rc = alloc_ws(ws, total, s);
+    if (rc) return rc;
+    unsigned char* d = static_cast<unsigned char*>(ws.base);
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), o_meta_end, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        if (cplx)
+            stage_columns_kernel<double2><<<(unsigned)batch, 256, 0, s>>>(
+                reinterpret_cast<const double2*>(A), reinterpret_cast<const StageDesc*>(d + o_stage),
+                reinterpret_cast<double2*>(d + o_col));
+        else
+            stage_columns_kernel<double><<<(unsigned)batch, 256, 0, s>>>(
+                A, reinterpret_cast<const StageDesc*>(d + o_stage), reinterpret_cast<double*>(d + o_col));
+        e = cudaGetLastError();
+    }
+    for (size_t gi = 0; e == cudaSuccess && gi < P.groups.size(); ++gi) {
+        const GroupPlan& g = P.groups[gi];
+        FpLaunch L;
+        L.colT = reinterpret_cast<const double*>(d + o_col) + g.col_off;
+        L.partial = reinterpret_cast<double*>(d + o_part) + (size_t)pw * g.part_off;
+        L.mat_stride = g.mat_stride;
+        L.item_begin = 0;
+        L.item_end = (uint64_t)g.items;
+        L.ell = g.ell;
+        L.log2_chunks = g.log2_chunks;
+        e = cplx ? dispatch_c128(g.n, L, s) : dispatch_f64(g.n, L, s);
+    }
+    if (e == cudaSuccess) {
+        finalize_fp_kernel<<<(unsigned)batch, kFinalThreads, 0, s>>>(
+            reinterpret_cast<const double*>(d + o_part), reinterpret_cast<const FpFinal*>(d + o_fin), cplx ? 1 : 0,
+            out);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(ws.base, s);
+    if (e != cudaSuccess) return cuda_fail(e, cplx ? "perm_c128 launch" : "perm_f64 launch");
+    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+    return PERMX_OK;
+}
+
+}  // namespace permx
+
+namespace permx {
+cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t* colT, cudaStream_t s) {
+    StageDesc h{0, 0, n, ld};
+    StageDesc* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, sizeof h, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        stage_columns_kernel<uint32_t><<<1, 256, 0, s>>>(A, d, colT);
+        e = cudaGetLastError();
+    }
+    cudaError_t f = cudaFreeAsync(d, s);
+    return e != cudaSuccess ? e : f;
+}
+}  // namespace permx

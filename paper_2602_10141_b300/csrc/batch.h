@@ -1,0 +1,70 @@
+// Batch planning structures shared by batch.cu, schur.cpp and serve.cpp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace permx {
+
+enum class Field { C128 = 0, F64 = 1, MODP = 2 };
+
+struct StageDesc {          // one matrix to stage column-major (offsets in entries)
+    int64_t src;            // A + src: row-major n*n
+    int64_t dst;            // colT + dst: column j at + j*ld
+    int32_t n, ld;
+};
+
+struct ModpFinal {
+    uint32_t p, rfix;       // rfix = 2^(32(n-1)) mod p undoes the Montgomery factors
+    int32_t negate;         // (-1)^n
+    int32_t pad_;
+    int64_t out_index;
+};
+
+struct ModpFinalAt {
+    int64_t acc_index, out_index;
+    uint32_t p, rfix;
+    int32_t negate, pad_;
+};
+
+struct FpFinal {
+    int64_t first, count;   // partial slots of this matrix
+    int64_t out_index;
+    int32_t negate, pad_;
+};
+
+struct GroupPlan {
+    int n = 0, ell = 0, log2_chunks = 0, ld = 0;
+    int64_t mat_stride = 0;          // elements (uint32 or double) between matrices
+    int64_t col_off = 0;             // elements
+    int64_t first_mat = 0;           // index of the group's first matrix in plan order
+    int64_t items = 0;               // chunks in the group
+    int64_t partials_per_mat = 0;    // fp: partial slots per matrix
+    int64_t part_off = 0;            // fp: first partial slot of the group
+    std::vector<int64_t> mats;       // batch indices in plan order
+};
+
+struct BatchPlan {
+    Field field = Field::MODP;
+    int64_t batch = 0;
+    int64_t col_elems = 0;
+    int64_t total_partials = 0;
+    std::vector<GroupPlan> groups;
+};
+
+int validate_batch(const void* A, const int32_t* n, const int64_t* offset, int64_t batch, const void* out,
+                   int max_n);
+BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field);
+uint64_t plan_units(const BatchPlan& P);
+int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
+                   uint32_t* out, cudaStream_t s);
+cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t count, void* colT, cudaStream_t s);
+cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
+                               cudaStream_t s);
+cudaError_t launch_finalize_modp_at(const unsigned long long* acc, const ModpFinalAt* f, int64_t count, uint32_t* out,
+                                    cudaStream_t s);
+int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64_t batch, void* out, bool cplx,
+                 cudaStream_t s);
+
+}  // namespace permx

@@ -1,0 +1,114 @@
+// Internal definitions shared by the permx CUDA sources (not a public header).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "permx.h"
+
+namespace permx {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local last error, see perm_last_error)
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PERMX_CUDA(call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Chunk plan (paper §2.2: contiguous Gray-code blocks).  A chunk is L = 2^ell
+// consecutive Gray indices.  ell depends only on (n, field) so a matrix is
+// always cut the same way, whatever batch it is in.
+// ---------------------------------------------------------------------------
+int chunk_log2_modp(int n);
+int chunk_log2_fp(int n, bool cplx);
+
+// Padded column length: columns start on 16-byte boundaries.
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ constexpr int pad2(int n) { return (n + 1) & ~1; }
+
+// ---------------------------------------------------------------------------
+// Launch descriptors.  One launch covers a group of matrices that share n.
+// Batch mode (segs == nullptr): work item i (item_begin <= i < item_end) is
+// chunk (i & (chunks-1)) of matrix (i >> log2_chunks) of the group.
+// Segment mode (serving): item i belongs to the last segment s with
+// segs[s].item_start <= i and is chunk segs[s].chunk0 + (i - item_start) of
+// that segment's matrix, if below segs[s].chunk_end.  Segment starts are
+// aligned to min(chunks, 32) items so that a lane group never spans two
+// matrices and always holds the same chunks as in batch mode.
+// ---------------------------------------------------------------------------
+struct SegDesc {
+    int64_t item_start;            // first launch item of the segment
+    uint64_t chunk0, chunk_end;    // chunk range of the matrix advanced by this segment
+    int64_t col_off;               // staged columns at colT + col_off
+    int64_t out_off;               // modp: accumulator acc[out_off]; fp: partial slot of chunk 0
+    uint32_t p, pinv;              // modp only
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int find_segment(const SegDesc* __restrict__ segs, int nsegs, uint64_t item) {
+    int lo = 0, hi = nsegs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)__ldg(reinterpret_cast<const long long*>(&segs[mid].item_start)) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+
+struct ModpLaunch {
+    const uint32_t* colT;          // group columns: matrix m at colT + m*mat_stride, column j at + j*pad4(n)
+    const uint32_t* p;             // per-matrix prime
+    const uint32_t* pinv;          // per-matrix p^{-1} mod 2^32
+    unsigned long long* acc;       // per-matrix accumulator (sum of partials, each < p)
+    int64_t mat_stride;            // elements between matrices
+    uint64_t item_begin, item_end; // item range of this launch
+    uint64_t k_lo, k_hi;           // Gray-index window applied to every chunk (0, 2^n for a full permanent)
+    int ell;                       // log2 chunk length
+    int log2_chunks;               // log2 chunks per matrix (n - ell)
+    const SegDesc* segs = nullptr; // segment mode when non-null
+    int nsegs = 0;
+};
+
+struct FpLaunch {
+    const double* colT;            // group columns (complex: interleaved), matrix m at colT + m*mat_stride
+    double* partial;               // per item: (s, c) for real, (s_re, c_re, s_im, c_im) for complex
+    int64_t mat_stride;            // doubles between matrices
+    uint64_t item_begin, item_end;
+    int ell;
+    int log2_chunks;
+    const SegDesc* segs = nullptr; // segment mode when non-null
+    int nsegs = 0;
+};
+
+template <int N> cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s);
+template <int N> cudaError_t launch_f64(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> cudaError_t launch_c128(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> int blocks_per_sm_modp();
+template <int N> int blocks_per_sm_f64();
+template <int N> int blocks_per_sm_c128();
+
+// dispatch on runtime n (defined in dispatch.cu)
+cudaError_t dispatch_modp(int n, const ModpLaunch& L, cudaStream_t s);
+cudaError_t dispatch_f64(int n, const FpLaunch& L, cudaStream_t s);
+cudaError_t dispatch_c128(int n, const FpLaunch& L, cudaStream_t s);
+
+constexpr int kRyserThreads = 256;
+
+int sm_count();
+
+// host helpers (field.cpp)
+bool is_prime_u32(uint32_t p);
+uint32_t inv_mod_2_32(uint32_t p);                  // p odd: p * inv = 1 (mod 2^32)
+uint32_t pow_mod(uint32_t b, uint64_t e, uint32_t p);
+
+}  // namespace permx

@@ -1,0 +1,164 @@
+// Gray-code Ryser over F_p (paper §2.1 field, §2.2 Gray-code blocks).
+//
+// One thread owns one chunk of L = 2^ell consecutive Gray indices k of one
+// matrix.  At the chunk start it forms the row sums r_i = sum_{j in S} a_ij of
+// S = k ^ (k >> 1) from scratch; then every step k -> k+1 toggles column
+// j = ctz(k+1): r_i += a_ij if that bit of S turns on, r_i -= a_ij if it turns
+// off.  The term prod_i r_i enters with sign (-1)^{|S_k|} = (-1)^k, so even
+// and odd k are summed separately (E, O) and the chunk contributes E - O.
+//
+// Arithmetic: residues are uint32 in [0, p), p < 2^31.  Modular add/sub use
+// one add and an unsigned min.  Products use Montgomery reduction with
+// R = 2^32 (T = a*b; m = T*p^{-1} mod R; (T - m p)/R = hi(T) - hi(m p) in
+// (-p, p)).  The product of n row sums by n-1 Montgomery steps carries
+// R^{-(n-1)}; the finalize step multiplies it back.  Partial sums are summed in
+// uint64 without reduction (L * 2^31 < 2^64).
+#pragma once
+#include "common.cuh"
+
+namespace permx {
+
+__device__ __forceinline__ uint32_t mod_add(uint32_t r, uint32_t a, uint32_t p) {
+    uint32_t s = r + a;           // < 2p < 2^32
+    return min(s, s - p);         // s - p wraps to > p when s < p
+}
+__device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p) {
+    uint32_t d = r - a;           // wraps to > 2^31 > p when r < a
+    return min(d, d + p);
+}
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+    uint64_t T = (uint64_t)a * b;
+    uint32_t m = (uint32_t)T * pinv;
+    uint32_t mh = __umulhi(m, p);
+    uint32_t r = (uint32_t)(T >> 32) - mh;   // true value in (-p, p)
+    return min(r, r + p);
+}
+
+// prod_i r_i * R^{-(N-1)} by a balanced tree (depth log2 N) for ILP.  The
+// level loop has a fixed trip count so that, fully unrolled, every index is a
+// compile-time constant and v[] stays in registers.
+template <int N>
+__device__ __forceinline__ uint32_t prod_tree(const uint32_t (&r)[N], uint32_t p, uint32_t pinv) {
+    static_assert(N <= 64, "tree depth");
+    uint32_t v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = r[i];
+#pragma unroll
+    for (int lvl = 0; lvl < 6; ++lvl) {
+        const int w = (N + (1 << lvl) - 1) >> lvl;   // live values at this level
+        if (w > 1) {
+#pragma unroll
+            for (int i = 0; i < N / 2; ++i)
+                if (i < w / 2) v[i] = mont_mul(v[2 * i], v[2 * i + 1], p, pinv);
+            if (w & 1) v[w / 2] = v[w - 1];
+        }
+    }
+    return v[0];
+}
+
+template <int N, bool SUB>
+__device__ __forceinline__ void apply_column(uint32_t (&r)[N], const uint32_t* __restrict__ cj, uint32_t p) {
+    constexpr int NP = pad4(N);
+    const uint4* c4 = reinterpret_cast<const uint4*>(cj);
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+        uint4 v = __ldg(c4 + q);
+        uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (4 * q + e < N) r[4 * q + e] = SUB ? mod_sub(r[4 * q + e], a[e], p) : mod_add(r[4 * q + e], a[e], p);
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRyserThreads, 2) ryser_modp_kernel(const ModpLaunch L) {
+    constexpr int NP = pad4(N);
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    // lanes holding chunks of the same matrix form aligned groups of G lanes
+    const int G = L.log2_chunks >= 5 ? 32 : (1 << L.log2_chunks);
+    // warp-aligned loop: every lane of a warp runs the same number of iterations
+    for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         base < L.item_end; base += stride) {
+        const uint64_t item = base + lane;
+        // decode the item: matrix columns, prime, accumulator and chunk index
+        bool valid = item < L.item_end;
+        const uint32_t* col = L.colT;
+        unsigned long long* acc = L.acc;
+        uint32_t p = 1, pinv = 1;
+        uint64_t c = 0;
+        if (valid) {
+            if (L.segs) {
+                const SegDesc& sg = L.segs[find_segment(L.segs, L.nsegs, item)];
+                c = sg.chunk0 + (item - (uint64_t)sg.item_start);
+                valid = c < sg.chunk_end;
+                col += sg.col_off;
+                acc += sg.out_off;
+                p = sg.p;
+                pinv = sg.pinv;
+            } else {
+                const int64_t m = (int64_t)(item >> L.log2_chunks);
+                c = item & chunk_mask;
+                col += m * L.mat_stride;
+                acc += m;
+                p = __ldg(L.p + m);
+                pinv = __ldg(L.pinv + m);
+            }
+        }
+        uint32_t part = 0;
+        uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+        ks = ks > L.k_lo ? ks : L.k_lo;
+        ke = ke < L.k_hi ? ke : L.k_hi;
+        if (valid && ks < ke) {
+            // chunk start: row sums of S = gray(ks) from scratch
+            uint32_t r[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) r[i] = 0;
+            const uint64_t S0 = ks ^ (ks >> 1);
+#pragma unroll 1
+            for (int j = 0; j < N; ++j)
+                if ((S0 >> j) & 1) apply_column<N, false>(r, col + j * NP, p);
+
+            unsigned long long E = 0, O = 0;
+            {
+                uint32_t t = prod_tree<N>(r, p, pinv);
+                if (ks & 1) O += t; else E += t;
+            }
+            for (uint64_t k = ks + 1; k < ke; ++k) {
+                const int j = __ffsll((long long)k) - 1;             // column toggled between k-1 and k
+                const uint32_t* cj = col + j * NP;
+                if ((k >> (j + 1)) & 1) apply_column<N, true>(r, cj, p);   // bit j of gray(k) turns off
+                else apply_column<N, false>(r, cj, p);                     // bit j turns on
+                uint32_t t = prod_tree<N>(r, p, pinv);
+                if (k & 1) O += t; else E += t;
+            }
+            const uint32_t e = (uint32_t)(E % p), o = (uint32_t)(O % p);
+            part = (e >= o) ? (e - o) : (e + p - o);
+        }
+        // sum the group's partials mod p (all lanes of a group share m and p)
+        for (int d = 1; d < G; d <<= 1) part = mod_add(part, __shfl_xor_sync(0xffffffffu, part, d), p);
+        if ((lane & (G - 1)) == 0 && valid && part) atomicAdd(acc, (unsigned long long)part);
+    }
+}
+
+template <int N>
+cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s) {
+    ryser_modp_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+template <int N>
+int blocks_per_sm_modp() {
+    static int cached = -1;
+    if (cached < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_modp_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+}  // namespace permx

@@ -1,0 +1,47 @@
+// Schur-permanent driver structures (schur.cpp) and the single-matrix F_p
+// range runner shared with the serving loop.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "field.h"
+
+namespace permx {
+
+cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t* colT, cudaStream_t s);
+
+struct ModpRange {                    // one staged F_p matrix, summed over Gray-index windows
+    int n = 0, ell = 0, ld = 0;
+    uint32_t p = 0;
+    cudaStream_t s = nullptr;
+    uint32_t* col = nullptr;          // column-major copy + accumulator
+    uint32_t* params = nullptr;       // {p, p^-1 mod 2^32}
+    unsigned long long* acc = nullptr;
+    int init(const uint32_t* A_dev, int n, uint32_t p, cudaStream_t s);
+    int run(uint64_t k0, uint64_t k1, uint32_t* residue);   // synchronous
+    void release();
+};
+
+struct SchurState {
+    int n = 0;
+    std::vector<uint32_t> primes;     // main primes then the check prime
+    std::vector<uint32_t> done;       // residues of perm(S_n) for the finished primes, in order
+    uint64_t cursor = 0;              // next Gray index of the current prime
+    uint32_t partial = 0;             // signed Ryser sum over [0, cursor) mod p (no (-1)^n)
+};
+
+struct SchurResult {
+    std::vector<uint32_t> primes, residues;
+    Big magnitude;
+    bool negative = false;
+};
+
+int write_checkpoint(const std::string& path, const SchurState& st);
+int read_checkpoint(const std::string& path, SchurState& st);
+int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subsets, int64_t max_slices,
+                  SchurResult& res);
+
+}  // namespace permx

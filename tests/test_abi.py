@@ -1,0 +1,94 @@
+"""The C-ABI library loads without a GPU, exports every function the public
+header declares, and its host-side helpers (primes, roots, Schur residues,
+CRT; paper §2.1) agree with the oracle's independent Python versions."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "permx.h")
+LIB = os.path.join(ROOT, "paper_2602_10141_b300", "libpermx.so")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s+(\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def px():
+    if not os.path.exists(LIB):
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("_b", os.path.join(ROOT, "paper_2602_10141_b300", "build.py"))
+        b = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(b)
+        b.build()
+    import paper_2602_10141_b300 as px
+    return px
+
+
+def test_header_symbols_exported(px):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(LIB)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string(px):
+    assert "sm_103a" in px.version()
+    with pytest.raises(px.PermxError) as e:
+        px.perm_primes_1_mod_n(0, 3)
+    assert e.value.code == px.PERMX_EINVAL and px.last_error()
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 12, 33, 43, 48])
+def test_primes_match_oracle(px, n):
+    assert px.perm_primes_1_mod_n(n, 7) == O.primes_1_mod_n(n, 7)
+    assert px.perm_primes_1_mod_n(n, 3, skip=4) == O.primes_1_mod_n(n, 3, skip=4)
+
+
+@pytest.mark.parametrize("n", [3, 9, 16, 33, 43])
+def test_roots_and_residues_match_oracle(px, n):
+    for p in O.primes_1_mod_n(n, 3):
+        g = px.perm_primitive_root(p, n)
+        assert g == O.primitive_nth_root(p, n)
+        assert np.array_equal(px.perm_schur_residues(n, p, g), O.schur_residue_matrix(n, p, g))
+
+
+def test_crt_matches_oracle(px):
+    g = np.random.default_rng(5)
+    ps = O.primes_1_mod_n(43, 4)
+    M = int(np.prod([int(p) for p in ps], dtype=object))
+    for _ in range(200):
+        x = int(g.integers(-2 ** 62, 2 ** 62)) * int(g.integers(1, 2 ** 62))
+        x = ((x + M // 2) % M) - M // 2
+        if x > M // 2 or abs(x) >= 2 ** 127:
+            continue
+        res = [x % p for p in ps]
+        assert px.perm_crt(res, ps) == O.crt(res, ps) == x
+
+
+def test_prime_count_matches_bound(px):
+    for n in range(1, 49):
+        k = px.perm_schur_prime_count(n)
+        ps = O.primes_1_mod_n(n, k)
+        assert O.crt_modulus_suffices(n, ps)
+        if n >= 36 and n <= 43:
+            assert k == O.prime_count_for(n) == 5
+
+
+def test_invalid_helper_arguments(px):
+    for args in ((7, 4), (9, 2)):   # 7 != 1 (mod 4); 9 is not prime
+        with pytest.raises(px.PermxError):
+            px.perm_primitive_root(*args)
+    with pytest.raises(px.PermxError):
+        px.perm_crt([1, 2], [7, 7])
+    with pytest.raises(px.PermxError):
+        px.perm_schur_residues(0, 7, 2)

@@ -1,0 +1,274 @@
+"""CUDA path vs the oracle, element by element on seeded inputs (the C-ABI
+through the Python binding).  F_p and CRT results must be bit-exact; float64
+and complex128 results must meet the floating-point tolerance below."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import ENSEMBLES, ensemble, geodesic_cycle, random_residues, rng
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def fp_tolerance(ref, abs_terms, n):
+    """Pass bound for a float64 / complex128 result.
+
+    1e-9 relative, or the forward error bound of the Gray-code walk: every
+    term prod_i r_i carries at most ~n roundings in its product plus the
+    row-sum drift of a walk of <= 2^12 steps (a few dozen ulps), so
+    |error| <= 64 n u sum_S |prod_i r_i(S)|.  The second clause only matters
+    when the alternating sum cancels by many orders of magnitude."""
+    return max(1e-9 * abs(ref), 64 * n * U * abs_terms)
+
+
+@pytest.fixture(scope="module")
+def px():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2602_10141_b300 as px
+    return px
+
+
+def _dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.cuda()
+
+
+def _pack(mats):
+    n = [m.shape[0] for m in mats]
+    off = np.concatenate([[0], np.cumsum([k * k for k in n])[:-1]]).astype(np.int64)
+    flat = np.concatenate([m.reshape(-1) for m in mats])
+    return flat, n, off
+
+
+def run_modp(px, mats, primes):
+    import torch
+    flat, n, off = _pack(mats)
+    A = _dev(flat.astype(np.int32))
+    out = torch.empty(len(mats), dtype=torch.int32, device="cuda")
+    px.perm_modp(A, n, off, primes, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+
+
+def run_fp(px, mats):
+    import torch
+    flat, n, off = _pack(mats)
+    cplx = np.iscomplexobj(flat)
+    A = _dev(flat)
+    out = torch.empty(len(mats), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+    (px.perm_c128 if cplx else px.perm_f64)(A, n, off, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# F_p: bit-exact
+# ---------------------------------------------------------------------------
+
+def test_modp_ragged_batch_bit_exact(px):
+    g = rng(1000)
+    primes = [2147483629, 2147483647, 65537, 3, 1000003]
+    mats, ps = [], []
+    for n in list(range(1, 25)) + [7, 13, 22, 24]:
+        p = primes[n % len(primes)]
+        mats.append(random_residues(n, p, g))
+        ps.append(p)
+    got = run_modp(px, mats, ps)
+    for A, p, v in zip(mats, ps, got):
+        n = A.shape[0]
+        ref = O.perm_modp_dp(A, p) if n > 10 else O.perm_modp_brute(A, p)
+        assert int(v) == ref, (n, p)
+
+
+def test_modp_edge_values(px):
+    # all zeros, all p-1, identity, the largest admissible prime
+    p = 2147483647
+    mats = [np.zeros((5, 5), np.uint32), np.full((9, 9), p - 1, np.uint32), np.eye(17, dtype=np.uint32),
+            np.full((1, 1), p - 1, np.uint32)]
+    got = run_modp(px, mats, [p] * len(mats))
+    for A, v in zip(mats, got):
+        assert int(v) == O.perm_modp_dp(A, p)
+
+
+@pytest.mark.parametrize("n", [25, 26])
+def test_modp_larger_sizes(px, n):
+    g = rng(1100 + n)
+    p = 2147483629
+    A = random_residues(n, p, g)
+    assert int(run_modp(px, [A], [p])[0]) == O.perm_modp_dp(A, p)
+
+
+def test_gray_range_partial_sums(px):
+    import torch
+    g = rng(1200)
+    p = 2147483629
+    n = 30
+    A = random_residues(n, p, g)
+    dA = _dev(A.astype(np.int32))
+    for k0, k1 in ((0, 1 << 20), (123457, 123457 + 999983), ((1 << 29) - 77777, (1 << 29) + 1234567),
+                   ((1 << 30) - 4096, 1 << 30), (5, 5)):
+        assert px.perm_modp_gray_range(dA, n, p, k0, k1) == O.ryser_modp_gray_range(A, p, k0, k1)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n", [3, 5, 8, 12, 16, 19])
+def test_schur_residues_and_crt_small(px, n):
+    exact = O.schur_exact(n)
+    assert px.perm_schur_crt(n) == exact
+    for p in O.primes_1_mod_n(n, 2):
+        gr = O.primitive_nth_root(p, n)
+        S = O.schur_residue_matrix(n, p, gr)
+        assert int(run_modp(px, [S], [p])[0]) == exact % p
+
+
+def test_schur_n33_disjoint_prime_sets(px):
+    # 5 primes just below 2^31 (plus a check prime inside the library); a second,
+    # disjoint set of 5 primes must reconstruct the same integer
+    n = 33
+    v, primes, res = px.perm_schur_crt_ex(n, 5)
+    assert primes == O.primes_1_mod_n(n, 6)
+    assert O.crt(res[:5], primes[:5]) == v
+    assert v * v <= n ** n
+    other = O.primes_1_mod_n(n, 5, skip=6)
+    gs = [O.primitive_nth_root(p, n) for p in other]
+    got = run_modp(px, [O.schur_residue_matrix(n, p, gg) for p, gg in zip(other, gs)], other)
+    assert O.crt([int(x) for x in got], other) == v
+    # Galois invariance: another primitive root gives the same residue
+    p = other[0]
+    g2 = pow(gs[0], 2, p)
+    assert int(run_modp(px, [O.schur_residue_matrix(n, p, g2)], [p])[0]) == int(got[0])
+
+
+def test_modp_invalid_arguments(px):
+    import torch
+    A = torch.zeros(16, dtype=torch.int32, device="cuda")
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for n, p in ((0, 7), (49, 2147483629), (4, 2147483648 - 1 + 2), (4, 9), (4, 2)):
+        with pytest.raises(px.PermxError) as e:
+            px.perm_modp(A, [n], [0], [p], out)
+        assert e.value.code == px.PERMX_EINVAL
+    with pytest.raises(px.PermxError):
+        px.perm_modp_host(np.full((2, 2), 11, np.uint32), [2], [0], [11])
+
+
+# ---------------------------------------------------------------------------
+# float64 / complex128
+# ---------------------------------------------------------------------------
+
+def _check_fp(mats, got):
+    worst = 0.0
+    for A, v in zip(mats, got):
+        n = A.shape[0]
+        ref = O.perm_dp(A)
+        _, abs_terms = O.perm_ryser(A, with_abs=True) if n <= 18 else (None, None)
+        if abs_terms is None:
+            abs_terms = 0.0
+        err = abs(v - ref)
+        assert err <= fp_tolerance(ref, abs_terms, n), (n, v, ref, err)
+        if ref != 0:
+            worst = max(worst, err / abs(ref))
+    return worst
+
+
+@pytest.mark.parametrize("name", list(ENSEMBLES))
+def test_fp_ensembles_ragged(px, name):
+    mats = []
+    for n in list(range(1, 19)) + [9, 14]:
+        mats.append(ensemble(name, n, 1, seed=2000 + n)[0])
+    worst = _check_fp(mats, run_fp(px, mats))
+    assert worst < 1e-9
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_fp_larger_sizes(px, cplx):
+    # n = 20, 21: relative error against the error bound of float64 products; at
+    # these sizes the Haar permanent's terms cancel by ~1e8-1e9, so 1e-9 relative
+    # is at the edge of what float64 products can deliver
+    name = "haar_u" if cplx else "haar_o"
+    mats = [ensemble(name, n, 1, seed=2100 + n)[0] for n in (20, 21)]
+    got = run_fp(px, mats)
+    for A, v in zip(mats, got):
+        ref = O.perm_dp(A)
+        _, abs_terms = O.perm_ryser(A, with_abs=True)
+        assert abs(v - ref) <= fp_tolerance(ref, abs_terms, A.shape[0]), (A.shape[0], v, ref)
+
+
+def test_haar_unitary_n14_one_per_launch(px):
+    # 256 Haar-random U(14), seed 0, one matrix per launch
+    mats = ensemble("haar_u", 14, 256, seed=0)
+    for A in mats[::16]:
+        v = run_fp(px, [A])[0]
+        ref = O.perm_dp(A)
+        assert abs(v - ref) <= 1e-9 * abs(ref)
+
+
+def test_geodesic_midpoints(px):
+    # paper §4.1 table: midpoint of the cycle geodesic; even n -> 0
+    ns = [5, 7, 9, 11, 13, 15, 17]
+    mats = [geodesic_cycle(n, 0.5, "circulant") for n in ns] + [geodesic_cycle(n, 0.5, "principal") for n in ns]
+    got = run_fp(px, mats)
+    for A, v in zip(mats, got):
+        n = A.shape[0]
+        ref = O.perm_dp(A)
+        _, abs_terms = O.perm_ryser(A, with_abs=True)
+        assert abs(v - ref) <= fp_tolerance(ref, abs_terms, n)
+        pred = 2 * math.exp(-n) * (1 + 1 / (3 * n))
+        assert abs(abs(v) / pred - 1) <= 1.0 / n ** 2
+    even = run_fp(px, [geodesic_cycle(n, 0.5, "circulant") for n in (6, 10, 14)])
+    assert np.all(np.abs(even) <= 1e-13)
+
+
+def test_fp_identity_ones_and_hermitian(px):
+    mats = [np.eye(12, dtype=complex), np.ones((10, 10), complex), np.ones((12, 12))]
+    got = run_fp(px, mats[:2])
+    assert got[0] == 1.0
+    assert got[1] == math.factorial(10)
+    assert run_fp(px, mats[2:])[0] == math.factorial(12)
+    # Hermitian => real permanent (paper §5, Proposition); the computed imaginary part is
+    # rounding error and must stay within the float64 error bound of the walk
+    H = ensemble("gue", 15, 4, seed=5)
+    for A, v in zip(H, run_fp(px, list(H))):
+        _, abs_terms = O.perm_ryser(A, with_abs=True)
+        assert abs(v.imag) <= fp_tolerance(0.0, abs_terms, 15)
+
+
+def test_fp_alone_equals_in_mix(px):
+    # the same matrix alone and inside a ragged batch gives bit-identical results
+    A = ensemble("haar_u", 16, 1, seed=77)[0]
+    B = ensemble("ginibre_r", 15, 1, seed=78)[0]
+    alone = run_fp(px, [A])[0]
+    mix = run_fp(px, [ensemble("haar_u", 9, 1, seed=1)[0], A] + list(ensemble("haar_u", 16, 5, seed=2)) + [A])
+    assert mix[1] == alone and mix[-1] == alone
+    alone_r = run_fp(px, [B])[0]
+    mix_r = run_fp(px, list(ensemble("goe", 12, 3, seed=3)) + [B])
+    assert mix_r[-1] == alone_r
+
+
+def test_host_variants_match_device(px):
+    mats = [ensemble("haar_u", n, 1, seed=3000 + n)[0] for n in (4, 11, 15)]
+    flat, n, off = _pack(mats)
+    host = px.perm_c128_host(flat, n, off)
+    dev = run_fp(px, mats)
+    assert np.array_equal(host, dev)
+    p = 2147483629
+    g = rng(9)
+    rm = [random_residues(k, p, g) for k in (3, 12, 20)]
+    flat, n, off = _pack(rm)
+    host = px.perm_modp_host(flat, n, off, [p] * 3)
+    assert [int(x) for x in host] == [O.perm_modp_dp(A, p) for A in rm]
+
+
+def test_fp_invalid_arguments(px):
+    import torch
+    A = torch.zeros(33 * 33, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for n in (0, 33, -1):
+        with pytest.raises(px.PermxError) as e:
+            px.perm_f64(A, [n], [0], out)
+        assert e.value.code == px.PERMX_EINVAL
