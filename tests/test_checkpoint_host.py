@@ -1,0 +1,37 @@
+"""Checkpoint files are validated on the host before any GPU work: a corrupt
+file or one from a different run is rejected (no GPU needed)."""
+import pytest
+
+
+@pytest.fixture(scope="module")
+def px():
+    import paper_2602_10141_b300 as px
+    return px
+
+
+def test_corrupt_checkpoint_rejected(px, tmp_path):
+    ck = tmp_path / "bad.ckpt"
+    ck.write_text("permx-schur-ckpt 1\nn 19\nprimes 3 1 2 3\ndone 0\ncursor 0 0\nsum 0000000000000000\n")
+    with pytest.raises(px.PermxError) as e:
+        px.perm_schur_crt_ex(19, 0, str(ck))
+    assert e.value.code == px.PERMX_EIO
+    ck.write_text("garbage")
+    with pytest.raises(px.PermxError) as e:
+        px.perm_schur_crt_ex(19, 0, str(ck))
+    assert e.value.code == px.PERMX_EIO
+
+
+def test_checkpoint_from_other_run_rejected(px, tmp_path):
+    # a well-formed file (valid checksum) written for n = 17 is refused for n = 19
+    import hashlib  # noqa: F401
+    body = "permx-schur-ckpt 1\nn 17\nprimes 2 2147483647 2147483629\ndone 0\ncursor 0 0\n"
+    h = 1469598103934665603
+    for c in body.encode():
+        h ^= c
+        h = (h * 1099511628211) % (1 << 64)
+    ck = tmp_path / "other.ckpt"
+    ck.write_text(body + "sum %016x\n" % h)
+    with pytest.raises(px.PermxError) as e:
+        px.perm_schur_crt_ex(19, 0, str(ck))
+    assert e.value.code == px.PERMX_EINVAL
+    assert "different run" in px.last_error()

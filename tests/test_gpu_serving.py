@@ -1,0 +1,203 @@
+"""Continuous-batching server (serve_*): results equal the batched path bit for
+bit whether a request runs alone or in a mix, requests admitted while others
+run overlap with them, and admission limits behave."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import ensemble, geodesic_cycle, random_residues, rng
+
+pytestmark = pytest.mark.gpu
+
+
+class Server:
+    def __init__(self, px, **cfg):
+        self.px = px
+        self.lib = px._lib
+        self.lib.serve_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        self.lib.serve_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
+        self.lib.serve_poll_timed.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64)]
+        self.lib.serve_drain.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        self.lib.serve_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        self.lib.serve_destroy.argtypes = [ctypes.c_void_p]
+        buf = bytearray(40)
+        vals = [cfg.get("max_requests", 0), cfg.get("max_resident", 0)]
+        import struct
+        struct.pack_into("<iiqqii", buf, 0, vals[0], vals[1], cfg.get("device_bytes", 0),
+                         cfg.get("chunks_per_step", 0), 0, cfg.get("plain_fifo", 0))
+        self._cfg = (ctypes.c_char * 40).from_buffer(buf)
+        self.h = ctypes.c_void_p()
+        assert self.lib.serve_create(ctypes.addressof(self._cfg), ctypes.byref(self.h)) == 0, px.last_error()
+
+    def submit(self, A, field, p=0):
+        if field == 2:
+            buf = np.ascontiguousarray(A, np.uint32)
+        elif field == 0:
+            buf = np.ascontiguousarray(A, np.complex128)
+        else:
+            buf = np.ascontiguousarray(A, np.float64)
+        t = ctypes.c_uint64()
+        rc = self.lib.serve_submit(self.h, field, A.shape[0], buf.ctypes.data, p, ctypes.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket, field):
+        res = (ctypes.c_char * 16)()
+        done, ts, td = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = self.lib.serve_poll_timed(self.h, ticket, res, ctypes.byref(done), ctypes.byref(ts), ctypes.byref(td))
+        if rc or not done.value:
+            return rc, None, None
+        raw = bytes(res)
+        if field == 0:
+            v = complex(*np.frombuffer(raw, np.float64, 2))
+        elif field == 1:
+            v = float(np.frombuffer(raw[:8], np.float64)[0])
+        else:
+            v = int(np.frombuffer(raw[:4], np.uint32)[0])
+        return 0, v, (td.value - ts.value) * 1e-9
+
+    def wait(self, tickets, timeout=120.0):
+        out = {}
+        t0 = time.time()
+        while len(out) < len(tickets):
+            for t, f in tickets:
+                if t in out:
+                    continue
+                rc, v, lat = self.poll(t, f)
+                assert rc == 0, self.px.last_error()
+                if v is not None:
+                    out[t] = (v, lat)
+            assert time.time() - t0 < timeout
+            time.sleep(0.0005)
+        return out
+
+    def stats(self):
+        s = (ctypes.c_int64 * 5)()
+        assert self.lib.serve_stats(self.h, s) == 0
+        return list(s)
+
+    def close(self):
+        self.lib.serve_destroy(self.h)
+
+
+def _batched(px, A, field, p=0):
+    import torch
+    if field == 2:
+        o = torch.empty(1, dtype=torch.int32, device="cuda")
+        px.perm_modp(torch.from_numpy(np.ascontiguousarray(A).view(np.int32).reshape(-1)).cuda(), [A.shape[0]], [0],
+                     [p], o)
+        torch.cuda.synchronize()
+        return int(o.cpu().numpy()[0]) & 0xFFFFFFFF
+    cplx = field == 0
+    o = torch.empty(1, dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+    (px.perm_c128 if cplx else px.perm_f64)(torch.from_numpy(A.reshape(-1)).cuda(), [A.shape[0]], [0], o)
+    torch.cuda.synchronize()
+    return complex(o.cpu().numpy()[0]) if cplx else float(o.cpu().numpy()[0])
+
+
+@pytest.fixture(scope="module")
+def px():
+    import paper_2602_10141_b300 as px
+    return px
+
+
+def _mix(seed, count):
+    g = rng(seed)
+    reqs = []
+    for i in range(count):
+        kind = i % 4
+        if kind == 0:
+            n = int(g.integers(10, 17))
+            reqs.append((ensemble("haar_u", n, 1, seed=seed * 1000 + i)[0], 0, 0))
+        elif kind == 1:
+            n = int(g.integers(10, 17))
+            reqs.append((ensemble("goe", n, 1, seed=seed * 1000 + i)[0], 1, 0))
+        elif kind == 2:
+            n = int(g.choice([9, 11, 13, 15]))
+            t = int(g.integers(0, 201)) / 200
+            reqs.append((geodesic_cycle(n, t, "principal").astype(np.complex128), 0, 0))
+        else:
+            n = int(g.integers(16, 21))
+            p = O.primes_1_mod_n(n, 1)[0]
+            reqs.append((random_residues(n, p, g), 2, p))
+    return reqs
+
+
+@pytest.mark.parametrize("plain", [0, 1])
+def test_mixed_requests_equal_batched_path(px, plain):
+    S = Server(px, plain_fifo=plain)
+    try:
+        reqs = _mix(7, 40)
+        tickets = []
+        for A, f, p in reqs:
+            rc, t = S.submit(A, f, p)
+            assert rc == 0, px.last_error()
+            tickets.append((t, f))
+        res = S.wait(tickets)
+        for (A, f, p), (t, _) in zip(reqs, tickets):
+            v = res[t][0]
+            assert v == _batched(px, A, f, p), (A.shape[0], f)
+        # spot-check against the oracle
+        A, f, p = reqs[3]
+        assert res[tickets[3][0]][0] == O.perm_modp_dp(A, p)
+        A, f, p = reqs[0]
+        ref = O.perm_dp(A)
+        assert abs(res[tickets[0][0]][0] - ref) <= 1e-9 * abs(ref)
+    finally:
+        S.close()
+
+
+def test_arrivals_join_while_others_run(px):
+    # a long request is admitted first; short ones submitted while it runs finish before it
+    S = Server(px)
+    try:
+        big = ensemble("haar_u", 28, 1, seed=9)[0]
+        rc, tb = S.submit(big, 0)
+        assert rc == 0
+        time.sleep(0.01)
+        small = [ensemble("haar_u", 12, 1, seed=100 + i)[0] for i in range(20)]
+        ts = []
+        for A in small:
+            rc, t = S.submit(A, 0)
+            assert rc == 0
+            ts.append((t, 0))
+        res_small = S.wait(ts)
+        rc, v, _ = S.poll(tb, 0)
+        assert rc == 0
+        assert v is None, "the large request should still be running when the small ones are done"
+        res_big = S.wait([(tb, 0)])
+        assert res_big[tb][0] == _batched(px, big, 0)
+        for A, (t, _) in zip(small, ts):
+            assert res_small[t][0] == _batched(px, A, 0)
+        st = S.stats()
+        assert st[0] == st[1] == 21 and st[3] >= 2
+    finally:
+        S.close()
+
+
+def test_memory_bound_admission_and_limits(px):
+    # a device budget that holds only a few requests at once still completes all of them
+    S = Server(px, device_bytes=1 << 13, max_requests=8)
+    try:
+        reqs = [ensemble("ginibre_c", 14, 1, seed=200 + i)[0] for i in range(8)]
+        ts = []
+        for A in reqs:
+            rc, t = S.submit(A, 0)
+            assert rc == 0
+            ts.append((t, 0))
+        rc, _ = S.submit(reqs[0], 0)
+        assert rc == px.PERMX_EBUSY
+        res = S.wait(ts)
+        for A, (t, _) in zip(reqs, ts):
+            assert res[t][0] == _batched(px, A, 0)
+        rc, _, _ = S.poll(123456789, 0)
+        assert rc == px.PERMX_ENOTFOUND
+        rc, _ = S.submit(np.zeros((3, 3), np.uint32) + 7, 2, 7)
+        assert rc == px.PERMX_EINVAL   # entries must be below p
+    finally:
+        S.close()
