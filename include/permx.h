@@ -108,6 +108,25 @@ int perm_f64_host(const double* A, const int32_t* n, const int64_t* offset, int6
 int perm_modp_host(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
                    int64_t batch, uint32_t* out, void* stream);
 
+/* Allocation-free variant of perm_modp (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate memory during a call, e.g.
+ * because another allocator owns the device memory budget or because the
+ * call sits on a latency-critical path that must not enter an allocator).
+ * Same arguments, results and exactness as perm_modp, for at most
+ * PERMX_NOALLOC_MAX_BATCH matrices per call (any 1 <= n <= 48); larger
+ * batches are rejected with PERMX_EINVAL.  It calls no cudaMalloc/cudaFree
+ * and allocates no device memory: its intermediates live in one fixed
+ * device array of PERMX_NOALLOC_SCRATCH_BYTES bytes that every GPU loading
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps (other streams or threads on
+ * the same device) race and must be serialised by the caller. */
+#define PERMX_NOALLOC_MAX_BATCH 64
+#define PERMX_NOALLOC_SCRATCH_BYTES (1 << 20)
+int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
+                      int64_t batch, uint32_t* out, void* stream);
+
 /* Signed Ryser partial sum of one F_p matrix over a range of Gray indices
  * (paper §2.2: one contiguous Gray-code block):
  *     out = sum_{k0 <= k < k1} (-1)^{|S_k|} prod_i sum_{j in S_k} a_ij  mod p,

@@ -53,6 +53,7 @@ def _load() -> ctypes.CDLL:
         "perm_c128_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
         "perm_f64_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
         "perm_modp_host": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
+        "perm_modp_noalloc": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
         "perm_modp_gray_range": ([vp, i32, u32, u64, u64, P(u32), vp], ctypes.c_int),
         "perm_schur_crt": ([i32, i32, ctypes.c_char_p, P(i64), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "perm_schur_crt_ex": ([i32, i32, ctypes.c_char_p, u64, i64, P(i64), ctypes.c_char_p, ctypes.c_size_t,
@@ -138,6 +139,15 @@ def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out,
     n, offset, p = _i32(n), _i64(offset), _u32(p)
     _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                           _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def perm_modp_noalloc(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out, stream=None):
+    """perm_modp for callers that cannot allocate: at most 64 matrices per call,
+    intermediates in the library's fixed device array (see include/permx.h)."""
+    n, offset, p = _i32(n), _i64(offset), _u32(p)
+    _check(_lib.perm_modp_noalloc(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
+                                  _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
     return out
 
 

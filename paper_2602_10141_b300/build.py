@@ -34,7 +34,7 @@ INSTANCES = {
     "inst_f64.cu": [(1, 11), (12, 22), (23, 32)],
     "inst_c128.cu": [(1, 8), (9, 16), (17, 24), (25, 32)],
 }
-PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu"]
+PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu", "noalloc.cu"]
 PLAIN_CPP = ["api.cpp", "field.cpp", "schur.cpp", "serve.cpp"]
 
 
