@@ -18,20 +18,19 @@
 
 namespace permx {
 
-int chunk_log2_modp(int n) {
+int chunk_log2_modp(int bits) {
     // Enough chunks to fill the GPU for one large matrix (about 2^22 chunks),
     // at least 2^8 subsets per chunk so the O(n^2) chunk start stays < 1%.
-    int ell = n - 22;
-    int lo = n < 8 ? n : 8;
+    int ell = bits - 22;
+    int lo = bits < 8 ? bits : 8;
     return ell < lo ? lo : ell;
 }
 
-int chunk_log2_fp(int n, bool cplx) {
+int chunk_log2_fp(int bits) {
     // At most 2^12 steps per chunk (row-sum drift of an incremental walk grows
-    // like sqrt(L) ulps); at least 2^6 (or all of 2^n) for the chunk start cost.
-    (void)cplx;
-    int ell = n - 14;
-    int lo = n < 6 ? n : 6;
+    // like sqrt(L) ulps); at least 2^6 (or the whole walk) for the chunk start cost.
+    int ell = bits - 14;
+    int lo = bits < 6 ? bits : 6;
     if (ell < lo) ell = lo;
     if (ell > 12) ell = 12;
     return ell;
@@ -54,8 +53,36 @@ int sm_count() {
 // device kernels: staging and finalisation
 // ---------------------------------------------------------------------------
 
-// One block per matrix: colT[dst + j*ld + i] = A[src + i*n + j] (elements of
-// `W` 32-bit words each).
+// x_i = a_{i,n-1} - (1/2) sum_j a_ij for the Nijenhuis-Wilf form.
+// F_p: 1/2 = (p+1)/2 mod p.  Floating point: the row sum is compensated
+// (Neumaier), the halving is exact.
+__device__ __forceinline__ uint32_t x_entry(const uint32_t* __restrict__ row, int n, uint32_t p) {
+    uint64_t s = 0;
+    for (int j = 0; j < n; ++j) s += row[j];
+    const uint64_t hs = (s % p) * (uint64_t)((p + 1) / 2) % p;
+    return (uint32_t)(((uint64_t)row[n - 1] + p - hs) % p);
+}
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    const double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+__device__ __forceinline__ double x_entry(const double* __restrict__ row, int n, uint32_t) {
+    double s = 0.0, c = 0.0;
+    for (int j = 0; j < n; ++j) neumaier(s, c, row[j]);
+    return row[n - 1] - 0.5 * (s + c);
+}
+__device__ __forceinline__ double2 x_entry(const double2* __restrict__ row, int n, uint32_t) {
+    double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+    for (int j = 0; j < n; ++j) {
+        neumaier(sr, cr, row[j].x);
+        neumaier(si, ci, row[j].y);
+    }
+    return make_double2(row[n - 1].x - 0.5 * (sr + cr), row[n - 1].y - 0.5 * (si + ci));
+}
+
+// One block per matrix: colT[dst + j*ld + i] = A[src + i*n + j], padding
+// zeroed, and in the Nijenhuis-Wilf form the x column at colT[dst + n*ld + i].
 template <typename T>
 __global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
     const StageDesc s = d[blockIdx.x];
@@ -68,6 +95,9 @@ __global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* _
         const int j = e / (s.ld - n), i = n + e % (s.ld - n);
         colT[s.dst + (int64_t)j * s.ld + i] = T{};
     }
+    if (s.nw)
+        for (int i = threadIdx.x; i < s.ld; i += blockDim.x)
+            colT[s.dst + (int64_t)n * s.ld + i] = i < n ? x_entry(A + s.src + (int64_t)i * n, n, s.p) : T{};
 }
 
 __device__ __forceinline__ uint32_t mulmod_u64(uint64_t a, uint64_t b, uint32_t p) {
@@ -121,7 +151,7 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double sg = x.negate ? -1.0 : 1.0;
+        const double sg = (x.negate ? -1.0 : 1.0) * (x.twice ? 2.0 : 1.0);
         const double re = sg * (sh[0][0] + sh[1][0]);
         if (cplx) {
             const double im = sg * (sh[2][0] + sh[3][0]);
@@ -226,13 +256,15 @@ BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field) {
         GroupPlan g;
         g.n = kv.first;
         g.mats = std::move(kv.second);
-        g.ell = field == Field::MODP ? chunk_log2_modp(g.n) : chunk_log2_fp(g.n, field == Field::C128);
-        g.log2_chunks = g.n - g.ell;
+        g.nw = 1;
+        const int bits = walk_bits(g.n, g.nw);
+        g.ell = field == Field::MODP ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+        g.log2_chunks = bits - g.ell;
         if (field == Field::MODP) g.ld = pad4(g.n);
         else if (field == Field::F64) g.ld = pad2(g.n);
         else g.ld = g.n;                          // complex entries are 16 bytes already
         const int words = field == Field::C128 ? 2 : 1;   // doubles (fp) or uint32 (modp) per entry
-        g.mat_stride = (int64_t)g.n * g.ld * words;
+        g.mat_stride = (int64_t)(g.n + g.nw) * g.ld * words;
         g.col_off = col_off;
         g.first_mat = mat_index;
         g.items = (int64_t)g.mats.size() << g.log2_chunks;
@@ -278,12 +310,13 @@ int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, c
     for (auto& g : P.groups) {
         for (size_t q = 0; q < g.mats.size(); ++q) {
             const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
-            stage[m] = StageDesc{offset[b], g.col_off + (int64_t)q * g.mat_stride, g.n, g.ld};
+            stage[m] = StageDesc{offset[b], g.col_off + (int64_t)q * g.mat_stride, g.n, g.ld, p[b], g.nw};
             pp[m] = p[b];
             pinv[m] = inv_mod_2_32(p[b]);
             fin[m].p = p[b];
             fin[m].rfix = pow_mod((uint32_t)(((uint64_t)1 << 32) % p[b]), (uint64_t)(g.n - 1), p[b]);
-            fin[m].negate = g.n & 1;
+            if (g.nw) fin[m].rfix = (uint32_t)((uint64_t)fin[m].rfix * 2 % p[b]);
+            fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
             fin[m].out_index = b;
         }
     }
@@ -323,9 +356,10 @@ int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, c
         L.item_begin = 0;
         L.item_end = (uint64_t)g.items;
         L.k_lo = 0;
-        L.k_hi = (uint64_t)1 << g.n;
+        L.k_hi = (uint64_t)1 << walk_bits(g.n, g.nw);
         L.ell = g.ell;
         L.log2_chunks = g.log2_chunks;
+        L.nw = g.nw;
         e = dispatch_modp(g.n, L, s);
     }
     if (e == cudaSuccess) {
@@ -350,10 +384,11 @@ int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64
         for (size_t q = 0; q < g.mats.size(); ++q) {
             const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
             // staging works on entries of w doubles: offsets in entries
-            stage[m] = StageDesc{offset[b], (g.col_off / w) + (int64_t)q * (g.mat_stride / w), g.n, g.ld};
+            stage[m] = StageDesc{offset[b], (g.col_off / w) + (int64_t)q * (g.mat_stride / w), g.n, g.ld, 0u, g.nw};
             fin[m].first = g.part_off + (int64_t)q * g.partials_per_mat;
             fin[m].count = g.partials_per_mat;
-            fin[m].negate = g.n & 1;
+            fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
+            fin[m].twice = g.nw;
             fin[m].out_index = b;
         }
     }
@@ -393,6 +428,7 @@ int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64
         L.item_end = (uint64_t)g.items;
         L.ell = g.ell;
         L.log2_chunks = g.log2_chunks;
+        L.nw = g.nw;
         e = cplx ? dispatch_c128(g.n, L, s) : dispatch_f64(g.n, L, s);
     }
     if (e == cudaSuccess) {
@@ -410,8 +446,9 @@ int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64
 }  // namespace permx
 
 namespace permx {
-cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t* colT, cudaStream_t s) {
-    StageDesc h{0, 0, n, ld};
+cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t p, int nw, uint32_t* colT,
+                              cudaStream_t s) {
+    StageDesc h{0, 0, n, ld, p, nw};
     StageDesc* d = nullptr;
     cudaError_t e = cudaMallocAsync(&d, sizeof h, s);
     if (e != cudaSuccess) return e;

@@ -13,10 +13,12 @@ struct StageDesc {          // one matrix to stage column-major (offsets in entr
     int64_t src;            // A + src: row-major n*n
     int64_t dst;            // colT + dst: column j at + j*ld
     int32_t n, ld;
+    uint32_t p;             // F_p only: the prime (x column arithmetic)
+    int32_t nw;             // 1: also write x_i = a_{i,n-1} - (1/2) sum_j a_ij as column n
 };
 
 struct ModpFinal {
-    uint32_t p, rfix;       // rfix = 2^(32(n-1)) mod p undoes the Montgomery factors
+    uint32_t p, rfix;       // rfix = 2^(32(n-1)) mod p undoes the Montgomery factors (times 2 in NW form)
     int32_t negate;         // (-1)^n
     int32_t pad_;
     int64_t out_index;
@@ -31,11 +33,12 @@ struct ModpFinalAt {
 struct FpFinal {
     int64_t first, count;   // partial slots of this matrix
     int64_t out_index;
-    int32_t negate, pad_;
+    int32_t negate;         // multiply by -1
+    int32_t twice;          // multiply by 2 (Nijenhuis-Wilf form)
 };
 
 struct GroupPlan {
-    int n = 0, ell = 0, log2_chunks = 0, ld = 0;
+    int n = 0, ell = 0, log2_chunks = 0, ld = 0, nw = 1;
     int64_t mat_stride = 0;          // elements (uint32 or double) between matrices
     int64_t col_off = 0;             // elements
     int64_t first_mat = 0;           // index of the group's first matrix in plan order

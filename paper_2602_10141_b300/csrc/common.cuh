@@ -25,11 +25,20 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ---------------------------------------------------------------------------
 // Chunk plan (paper §2.2: contiguous Gray-code blocks).  A chunk is L = 2^ell
-// consecutive Gray indices.  ell depends only on (n, field) so a matrix is
-// always cut the same way, whatever batch it is in.
+// consecutive Gray indices of a walk over `bits` subset bits (n for plain
+// Ryser, n - 1 for the Nijenhuis-Wilf form below).  ell depends only on
+// (n, field, form), so a matrix is always cut the same way, whatever batch it
+// is in.
+//
+// Nijenhuis-Wilf form of Ryser's formula ("nw"): with
+//     x_i = a_{i,n-1} - (1/2) sum_j a_ij,
+//     perm(A) = (-1)^{n-1} 2 sum_{S subset {0..n-2}} (-1)^{|S|} prod_i (x_i + sum_{j in S} a_ij),
+// i.e. half the subsets of plain Ryser at the same cost per subset.  The
+// staged matrix then carries x as an extra column (index n).
 // ---------------------------------------------------------------------------
-int chunk_log2_modp(int n);
-int chunk_log2_fp(int n, bool cplx);
+int chunk_log2_modp(int bits);
+int chunk_log2_fp(int bits);
+inline int walk_bits(int n, int nw) { return nw ? n - 1 : n; }
 
 // Padded column length: columns start on 16-byte boundaries.
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
@@ -74,9 +83,10 @@ struct ModpLaunch {
     uint64_t item_begin, item_end; // item range of this launch
     uint64_t k_lo, k_hi;           // Gray-index window applied to every chunk (0, 2^n for a full permanent)
     int ell;                       // log2 chunk length
-    int log2_chunks;               // log2 chunks per matrix (n - ell)
+    int log2_chunks;               // log2 chunks per matrix (walk bits - ell)
     const SegDesc* segs = nullptr; // segment mode when non-null
     int nsegs = 0;
+    int nw = 0;                    // 1: Nijenhuis-Wilf form (x column at index n)
 };
 
 struct FpLaunch {
@@ -88,6 +98,7 @@ struct FpLaunch {
     int log2_chunks;
     const SegDesc* segs = nullptr; // segment mode when non-null
     int nsegs = 0;
+    int nw = 0;                    // 1: Nijenhuis-Wilf form (x column at index n)
 };
 
 template <int N> cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s);

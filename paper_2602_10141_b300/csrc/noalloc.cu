@@ -166,7 +166,7 @@ extern "C" int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int6
         L.pinv = reinterpret_cast<const uint32_t*>(scratch + kOffPinv) + k0;
         L.acc = reinterpret_cast<unsigned long long*>(scratch + kOffAcc) + k0;
         L.mat_stride = (int64_t)nn * pad4(nn);
-        L.ell = chunk_log2_modp(nn);
+        L.ell = chunk_log2_modp(nn);   // plain Ryser form: the walk covers all nn columns
         L.log2_chunks = nn - L.ell;
         L.item_begin = 0;
         L.item_end = (uint64_t)(k1 - k0) << L.log2_chunks;

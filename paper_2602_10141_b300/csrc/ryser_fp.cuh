@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_f64_kernel(const FpLau
             const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
             double r[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) r[i] = 0.0;
+            for (int i = 0; i < N; ++i) r[i] = L.nw ? col[N * NP + i] : 0.0;   // x_i or 0
             const uint64_t S0 = ks ^ (ks >> 1);
 #pragma unroll 1
             for (int j = 0; j < N; ++j) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_c128_kernel(const FpLa
             const double2* col = reinterpret_cast<const double2*>(cold);
             double2 r[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) r[i] = make_double2(0.0, 0.0);
+            for (int i = 0; i < N; ++i) r[i] = L.nw ? __ldg(col + N * N + i) : make_double2(0.0, 0.0);
             const uint64_t S0 = ks ^ (ks >> 1);
 #pragma unroll 1
             for (int j = 0; j < N; ++j) {

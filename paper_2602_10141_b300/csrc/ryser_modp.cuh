@@ -71,8 +71,12 @@ __device__ __forceinline__ void apply_column(uint32_t (&r)[N], const uint32_t* _
     }
 }
 
+#ifndef PERMX_MODP_MINB
+#define PERMX_MODP_MINB 2   // resident blocks of 256 threads per SM the register budget targets
+#endif
+
 template <int N>
-__global__ void __launch_bounds__(kRyserThreads, 2) ryser_modp_kernel(const ModpLaunch L) {
+__global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_kernel(const ModpLaunch L) {
     constexpr int NP = pad4(N);
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_modp_kernel(const Modp
             uint32_t r[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) r[i] = 0;
+            if (L.nw) apply_column<N, false>(r, col + N * NP, p);   // r_i = x_i
             const uint64_t S0 = ks ^ (ks >> 1);
 #pragma unroll 1
             for (int j = 0; j < N; ++j)

@@ -24,23 +24,27 @@ namespace permx {
 // ---------------------------------------------------------------------------
 // single-matrix F_p range runner
 // ---------------------------------------------------------------------------
-int ModpRange::init(const uint32_t* A_dev, int n_, uint32_t p_, cudaStream_t s_) {
+int ModpRange::init(const uint32_t* A_dev, int n_, uint32_t p_, int nw_, cudaStream_t s_) {
     n = n_;
     p = p_;
     s = s_;
-    ell = chunk_log2_modp(n);
+    nw = nw_;
+    bits = walk_bits(n, nw);
+    ell = chunk_log2_modp(bits);
     ld = pad4(n);
-    PERMX_CUDA(cudaMallocAsync(&col, sizeof(uint32_t) * (size_t)n * ld + 256, s));
-    acc = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(col) + ((sizeof(uint32_t) * (size_t)n * ld + 15) & ~size_t(15)));
+    const size_t words = (size_t)(n + nw) * ld;
+    PERMX_CUDA(cudaMallocAsync(&col, sizeof(uint32_t) * words + 256, s));
+    acc = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(col) + ((sizeof(uint32_t) * words + 15) & ~size_t(15)));
     PERMX_CUDA(cudaMallocAsync(&params, 256, s));
     const uint32_t hp[2] = {p, inv_mod_2_32(p)};
     PERMX_CUDA(cudaMemcpyAsync(params, hp, sizeof hp, cudaMemcpyHostToDevice, s));
-    PERMX_CUDA(stage_columns_u32(A_dev, n, ld, col, s));
+    PERMX_CUDA(stage_columns_u32(A_dev, n, ld, p, nw, col, s));
     return PERMX_OK;
 }
 
 int ModpRange::run(uint64_t k0, uint64_t k1, uint32_t* residue) {
-    // residue = sum_{k0<=k<k1} (-1)^k prod_i r_i(S_k)  mod p   (no (-1)^n)
+    // residue = sum_{k0<=k<k1} (-1)^k prod_i r_i(S_k)  mod p, with r_i(S) = sum_{j in S} a_ij
+    // (plus x_i in the Nijenhuis-Wilf form); no sign or factor of the formula applied
     *residue = 0;
     if (k0 >= k1) return PERMX_OK;
     PERMX_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
@@ -56,7 +60,8 @@ int ModpRange::run(uint64_t k0, uint64_t k1, uint32_t* residue) {
     L.k_lo = k0;
     L.k_hi = k1;
     L.ell = ell;
-    L.log2_chunks = n - ell;
+    L.log2_chunks = bits - ell;
+    L.nw = nw;
     PERMX_CUDA(dispatch_modp(n, L, s));
     unsigned long long h = 0;
     PERMX_CUDA(cudaMemcpyAsync(&h, acc, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -87,7 +92,7 @@ static uint64_t fnv1a(const std::string& s) {
 }
 
 static std::string ckpt_body(const SchurState& st) {
-    std::string b = "permx-schur-ckpt 1\n";
+    std::string b = "permx-schur-ckpt 2\n";
     b += "n " + std::to_string(st.n) + "\n";
     b += "primes " + std::to_string(st.primes.size());
     for (uint32_t p : st.primes) b += " " + std::to_string(p);
@@ -130,7 +135,7 @@ int read_checkpoint(const std::string& path, SchurState& st) {
     SchurState r;
     const char* c = body.c_str();
     int used = 0, np = 0, nd = 0;
-    if (std::sscanf(c, "permx-schur-ckpt 1\nn %d\nprimes %d%n", &r.n, &np, &used) != 2 || np < 1 ||
+    if (std::sscanf(c, "permx-schur-ckpt 2\nn %d\nprimes %d%n", &r.n, &np, &used) != 2 || np < 1 ||
         np > PERMX_MAX_PRIMES + 1)
         return fail(PERMX_EIO, "checkpoint " + path + " has a bad header");
     c += used;
@@ -186,9 +191,10 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
         }
     }
 
-    const uint64_t total = 1ull << n;
-    const int ell = chunk_log2_modp(n);
-    uint64_t slice = slice_subsets ? slice_subsets : (n <= 37 ? total : (1ull << 37));
+    // Nijenhuis-Wilf form: 2^(n-1) Gray indices per prime
+    const uint64_t total = 1ull << walk_bits(n, 1);
+    const int ell = chunk_log2_modp(walk_bits(n, 1));
+    uint64_t slice = slice_subsets ? slice_subsets : (n <= 38 ? total : (1ull << 37));
     const uint64_t Lc = 1ull << ell;
     slice = (slice + Lc - 1) / Lc * Lc;
 
@@ -211,7 +217,7 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
         e = cudaMemcpyAsync(dA, hA.data(), sizeof(uint32_t) * n * n, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync"); break; }
         ModpRange R;
-        rc = R.init(dA, n, p, s);
+        rc = R.init(dA, n, p, 1, s);
         while (rc == PERMX_OK && st.cursor < total) {
             if (max_slices > 0 && slices >= max_slices) { rc = PERMX_EAGAIN; break; }
             const uint64_t next = st.cursor + slice < total ? st.cursor + slice : total;
@@ -222,7 +228,9 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
             st.cursor = next;
             ++slices;
             if (st.cursor == total) {
-                st.done.push_back((n & 1) ? (st.partial ? p - st.partial : 0) : st.partial);
+                // perm = (-1)^(n-1) 2 sum
+                const uint32_t v = (uint32_t)((uint64_t)st.partial * 2 % p);
+                st.done.push_back((n & 1) ? v : (v ? p - v : 0));
                 st.cursor = 0;
                 st.partial = 0;
             }

@@ -11,16 +11,19 @@
 
 namespace permx {
 
-cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t* colT, cudaStream_t s);
+cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t p, int nw, uint32_t* colT,
+                              cudaStream_t s);
 
-struct ModpRange {                    // one staged F_p matrix, summed over Gray-index windows
-    int n = 0, ell = 0, ld = 0;
+// One staged F_p matrix, summed over windows of Gray indices.  nw = 0: plain
+// Ryser over 2^n subsets; nw = 1: Nijenhuis-Wilf form over 2^(n-1) subsets.
+struct ModpRange {
+    int n = 0, ell = 0, ld = 0, nw = 0, bits = 0;
     uint32_t p = 0;
     cudaStream_t s = nullptr;
     uint32_t* col = nullptr;          // column-major copy + accumulator
     uint32_t* params = nullptr;       // {p, p^-1 mod 2^32}
     unsigned long long* acc = nullptr;
-    int init(const uint32_t* A_dev, int n, uint32_t p, cudaStream_t s);
+    int init(const uint32_t* A_dev, int n, uint32_t p, int nw, cudaStream_t s);
     int run(uint64_t k0, uint64_t k1, uint32_t* residue);   // synchronous
     void release();
 };
@@ -30,7 +33,8 @@ struct SchurState {
     std::vector<uint32_t> primes;     // main primes then the check prime
     std::vector<uint32_t> done;       // residues of perm(S_n) for the finished primes, in order
     uint64_t cursor = 0;              // next Gray index of the current prime
-    uint32_t partial = 0;             // signed Ryser sum over [0, cursor) mod p (no (-1)^n)
+    uint32_t partial = 0;             // signed sum over Gray indices [0, cursor) mod p (Nijenhuis-Wilf form,
+                                      // without its factor 2 (-1)^(n-1))
 };
 
 struct SchurResult {

@@ -174,12 +174,14 @@ int grow_pinned(unsigned char** p, size_t* cap, size_t need) {
 
 void plan_request(Request* r) {
     const bool modp = r->field == PERMX_FIELD_MODP;
-    r->ell = modp ? chunk_log2_modp(r->n) : chunk_log2_fp(r->n, r->field == PERMX_FIELD_C128);
-    r->log2_chunks = r->n - r->ell;
+    // the batched path's plan: Nijenhuis-Wilf form, same chunking
+    const int bits = walk_bits(r->n, 1);
+    r->ell = modp ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+    r->log2_chunks = bits - r->ell;
     r->lg = r->log2_chunks >= 5 ? 5 : r->log2_chunks;
     r->chunks = 1ull << r->log2_chunks;
     r->ld = modp ? pad4(r->n) : r->field == PERMX_FIELD_F64 ? pad2(r->n) : r->n;
-    r->col_bytes = align256((size_t)r->n * r->ld * entry_bytes(r->field));
+    r->col_bytes = align256((size_t)(r->n + 1) * r->ld * entry_bytes(r->field));
     const size_t tail = modp ? 8 : (size_t)(r->chunks >> r->lg) * (r->field == PERMX_FIELD_C128 ? 32 : 16);
     r->bytes = r->col_bytes + align256(tail);
 }
@@ -199,7 +201,8 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
         for (Request* r : admitted) {
             std::memcpy(S->h_upload + o, r->host.data(), r->host.size());
             const int eb = entry_bytes(r->field);
-            sd[r->field].push_back(StageDesc{(int64_t)(o / eb), (int64_t)(r->arena_off / eb), r->n, r->ld});
+            sd[r->field].push_back(
+                StageDesc{(int64_t)(o / eb), (int64_t)(r->arena_off / eb), r->n, r->ld, r->p, 1});
             o += align256(r->host.size());
         }
         PERMX_CUDA(cudaMemcpyAsync(S->d_upload, S->h_upload, up, cudaMemcpyHostToDevice, st));
@@ -327,6 +330,7 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             M.log2_chunks = l.any->log2_chunks;
             M.segs = segs;
             M.nsegs = l.nseg;
+            M.nw = 1;
             e = dispatch_modp(l.n, M, st);
         } else {
             FpLaunch F;
@@ -339,6 +343,7 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             F.log2_chunks = l.any->log2_chunks;
             F.segs = segs;
             F.nsegs = l.nseg;
+            F.nw = 1;
             e = l.field == PERMX_FIELD_C128 ? dispatch_c128(l.n, F, st) : dispatch_f64(l.n, F, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "server step launch");
@@ -361,7 +366,8 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
                 x.out_index = (int64_t)fm.size();
                 x.p = r->p;
                 x.rfix = pow_mod((uint32_t)((1ull << 32) % r->p), (uint64_t)(r->n - 1), r->p);
-                x.negate = r->n & 1;
+                x.rfix = (uint32_t)((uint64_t)x.rfix * 2 % r->p);   // Nijenhuis-Wilf factor 2
+                x.negate = !(r->n & 1);                             // and sign (-1)^(n-1)
                 fm.push_back(x);
                 om.push_back(r);
             } else {
@@ -369,7 +375,8 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
                 FpFinal x{};
                 x.first = (r->arena_off + (int64_t)r->col_bytes) / (8 * pw);
                 x.count = (int64_t)(r->chunks >> r->lg);
-                x.negate = r->n & 1;
+                x.negate = !(r->n & 1);
+                x.twice = 1;
                 if (r->field == PERMX_FIELD_C128) {
                     x.out_index = (int64_t)fc.size();
                     fc.push_back(x);

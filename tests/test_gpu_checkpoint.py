@@ -29,7 +29,7 @@ def test_slice_limit_then_resume(px, tmp_path):
         px.perm_schur_crt_ex(n, 0, ck, slice_subsets=1 << 14, max_slices=7)
     assert e.value.code == px.PERMX_EAGAIN
     text = open(ck).read()
-    assert text.startswith("permx-schur-ckpt 1") and "cursor" in text
+    assert text.startswith("permx-schur-ckpt 2") and "cursor" in text
     v, primes, res = px.perm_schur_crt_ex(n, 0, ck, slice_subsets=1 << 14)
     assert v == O.schur_exact(n)
     # a finished checkpoint answers again without recomputation
