@@ -71,9 +71,23 @@ __device__ __forceinline__ void apply_column(uint32_t (&r)[N], const uint32_t* _
     }
 }
 
+#ifndef PERMX_MODP_PAIR_MAX_N
+#define PERMX_MODP_PAIR_MAX_N 40   // pairwise steps while the two copies fit the register budget
+#endif
 #ifndef PERMX_MODP_MINB
 #define PERMX_MODP_MINB 2   // resident blocks of 256 threads per SM the register budget targets
 #endif
+
+// Step into Gray index k (k >= 1): column j = ctz(k) enters the subset if bit
+// j+1 of k is clear, leaves it otherwise.
+template <int N>
+__device__ __forceinline__ void toggle_column(uint32_t (&r)[N], const uint32_t* __restrict__ col, uint64_t k,
+                                              uint32_t p) {
+    constexpr int NP = pad4(N);
+    const int j = __ffsll((long long)k) - 1;
+    if ((k >> (j + 1)) & 1) apply_column<N, true>(r, col + j * NP, p);
+    else apply_column<N, false>(r, col + j * NP, p);
+}
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_kernel(const ModpLaunch L) {
@@ -127,17 +141,31 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                 if ((S0 >> j) & 1) apply_column<N, false>(r, col + j * NP, p);
 
             unsigned long long E = 0, O = 0;
-            {
-                uint32_t t = prod_tree<N>(r, p, pinv);
-                if (ks & 1) O += t; else E += t;
+            uint64_t k = ks;
+            if (k & 1) {                       // a window may start on an odd index
+                O += prod_tree<N>(r, p, pinv);
+                ++k;
+                if (k < ke) toggle_column<N>(r, col, k, p);
             }
-            for (uint64_t k = ks + 1; k < ke; ++k) {
-                const int j = __ffsll((long long)k) - 1;             // column toggled between k-1 and k
-                const uint32_t* cj = col + j * NP;
-                if ((k >> (j + 1)) & 1) apply_column<N, true>(r, cj, p);   // bit j of gray(k) turns off
-                else apply_column<N, false>(r, cj, p);                     // bit j turns on
-                uint32_t t = prod_tree<N>(r, p, pinv);
-                if (k & 1) O += t; else E += t;
+            // pairs (k even, k+1): the step k -> k+1 toggles column 0; both
+            // products are formed from independent copies, which doubles the
+            // instruction-level parallelism of the product trees
+            while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke) {
+                uint32_t r2[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) r2[i] = r[i];
+                if ((k >> 1) & 1) apply_column<N, true>(r2, col, p);
+                else apply_column<N, false>(r2, col, p);
+                E += prod_tree<N>(r, p, pinv);
+                O += prod_tree<N>(r2, p, pinv);
+                k += 2;
+#pragma unroll
+                for (int i = 0; i < N; ++i) r[i] = r2[i];
+                if (k < ke) toggle_column<N>(r, col, k, p);
+            }
+            for (; k < ke; ++k) {              // remaining steps one at a time
+                if (k & 1) O += prod_tree<N>(r, p, pinv); else E += prod_tree<N>(r, p, pinv);
+                if (k + 1 < ke) toggle_column<N>(r, col, k + 1, p);
             }
             const uint32_t e = (uint32_t)(E % p), o = (uint32_t)(O % p);
             part = (e >= o) ? (e - o) : (e + p - o);
