@@ -47,6 +47,13 @@ def _rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_prime_skip(rank: int) -> int:
+    """Rank r of a weak-scaling run takes primes [5r, 5r + 5) of the descending
+    list of primes p = 1 (mod 33) below 2^31: disjoint sets, each enough for
+    the CRT bound, so every rank reconstructs perm(S_33) independently."""
+    return NPRIMES * rank
+
+
 def field_setup(n: int, count: int, skip: int):
     """Primes, roots and residue matrices through the library's host helpers."""
     import paper_2602_10141_b300 as px
@@ -194,12 +201,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: the same kernel over 2^30 Gray indices of S_33 mod one prime")
+    ap.add_argument("--workload", default="schur33",
+                    choices=["schur33", "haar14_plain", "ensembles_batched", "serving", "profile_fp", "schur_long"],
+                    help="schur33 is the headline; the others measure the plain, batched and served paths")
+    ap.add_argument("--ns", default="", help="schur_long: comma-separated n (default 36..43)")
+    ap.add_argument("--scale", type=float, default=0.02,
+                    help="ensembles_batched / serving: fraction of the full sample counts")
     args = ap.parse_args()
     rank, world, local = _rank_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.profile_case:
         return run_profile_case()
+    if args.workload != "schur33":
+        import bench_workloads
+        return bench_workloads.run(args)
 
     import torch
     import torch.distributed as dist
@@ -209,7 +225,7 @@ def main():
     import paper_2602_10141_b300 as px
 
     # every rank: its own 5 primes (disjoint sets), residue matrices resident in HBM
-    primes, mats = field_setup(N, NPRIMES, skip=NPRIMES * rank)
+    primes, mats = field_setup(N, NPRIMES, skip=rank_prime_skip(rank))
     flat = np.concatenate([m.reshape(-1) for m in mats]).astype(np.uint32)
     n_arr = np.full(NPRIMES, N, np.int32)
     off = np.arange(NPRIMES, dtype=np.int64) * N * N

@@ -1,0 +1,362 @@
+"""Secondary measurements for bench.py (--workload ...): the plain
+one-matrix-per-launch path, the batched ragged ensemble path and the
+continuous-batching server, each printed as one JSON line.
+
+* haar14_plain — 256 Haar-random U(14), complex128, seed 0: one call per
+  matrix (plain) against one batched call of all 256.
+* ensembles_batched — ragged batch of the six ensembles of paper §3-§5
+  (Haar U, GUE, complex Ginibre in complex128; Haar O, GOE, real Ginibre in
+  float64) at n in {8, 12, 16, 20, 23}, ``scale`` x 50,000 of each, generated
+  on the device; one batched call per field against one call per matrix on
+  a subsample; a seeded subsample is checked against the oracle.
+* serving — Poisson arrivals at 70 % of the measured capacity for a mix of
+  complex128 Haar n in [10, 26], float64 GOE n in [10, 26], complex128
+  cycle-geodesic points (odd n in [9, 25], t on a 201-point grid) and F_p
+  random matrices n in [16, 30]; p50/p99 latency and throughput for the
+  continuous-batching server and for the plain FIFO server on the same trace.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+import statistics
+import struct
+import time
+
+import numpy as np
+
+SIZES = (8, 12, 16, 20, 23)
+CPLX = ("haar_u", "gue", "ginibre_c")
+REAL = ("haar_o", "goe", "ginibre_r")
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def nominal_terms(ns):
+    return float(sum(n * 2.0 ** n for n in ns))
+
+
+def run(args):
+    if args.workload == "schur_long":
+        return schur_long(args)
+    if args.workload == "profile_fp":
+        return profile_fp(args)
+    if args.workload == "haar14_plain":
+        return haar14_plain(args)
+    if args.workload == "ensembles_batched":
+        return ensembles_batched(args)
+    if args.workload == "serving":
+        return serving(args)
+    raise ValueError(args.workload)
+
+
+def schur_long(args):
+    """Exact perm(S_n) for n = 36..43 (5 primes below 2^31 + 1 check prime each),
+    sliced into checkpointed kernel launches; one JSON line per n."""
+    import tempfile
+
+    import paper_2602_10141_b300 as px
+    ns = [int(x) for x in args.ns.split(",")] if args.ns else list(range(36, 44))
+    tmp = tempfile.mkdtemp(prefix="permx_schur_")
+    for n in ns:
+        ck = os.path.join(tmp, f"s{n}.ckpt")
+        t0 = time.perf_counter()
+        value, primes, residues = px.perm_schur_crt_ex(n, 0, ck)
+        dt = time.perf_counter() - t0
+        terms = len(primes) * n * 2.0 ** (n - 1)
+        print(json.dumps({"workload": "schur_long", "n": n, "perm_S_n": str(value), "seconds": dt,
+                          "primes": primes, "residues": residues, "check_prime": primes[-1],
+                          "evaluated_terms_per_s": terms / dt, "nominal_terms_per_s": 2 * terms / dt,
+                          "bound_ok": value * value <= n ** n}), flush=True)
+    return 0
+
+
+def profile_fp(args):
+    """Small case for ncu: 64 complex Ginibre and 64 real Ginibre matrices, n = 20."""
+    import torch
+
+    import paper_2602_10141_b300 as px
+    from workloads import ensemble
+    for name in ("ginibre_c", "ginibre_r"):
+        mats = ensemble(name, 20, 64, seed=3)
+        A = torch.from_numpy(mats.reshape(-1)).cuda()
+        cplx = np.iscomplexobj(mats)
+        out = torch.empty(64, dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+        for _ in range(2):
+            (px.perm_c128 if cplx else px.perm_f64)(A, [20] * 64, [i * 400 for i in range(64)], out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "64 x n=20 complex + 64 x n=20 real Ginibre", "arith": px.permx_get_fp_arith()}))
+    return 0
+
+
+def haar14_plain(args):
+    import torch
+
+    import oracle as O
+    import paper_2602_10141_b300 as px
+    from workloads import ensemble
+    mats = ensemble("haar_u", 14, 256, seed=0)
+    A = torch.from_numpy(mats.reshape(-1)).cuda()
+    out = torch.empty(256, dtype=torch.complex128, device="cuda")
+    n1 = np.array([14], np.int32)
+    offs = [np.array([i * 196], np.int64) for i in range(256)]
+    nb, ob = np.full(256, 14, np.int32), np.arange(256, dtype=np.int64) * 196
+
+    def plain():
+        for i in range(256):
+            px.perm_c128(A, n1, offs[i], out[i:i + 1])
+
+    def batched():
+        px.perm_c128(A, nb, ob, out)
+
+    res = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, b = _events(torch)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = statistics.median(ms)
+    got = out.cpu().numpy()
+    worst = max(abs(got[i] - O.perm_dp(mats[i])) / abs(O.perm_dp(mats[i])) for i in range(0, 256, 32))
+    terms = 256 * 14 * 2.0 ** 14
+    line = {"workload": "haar14_plain", "metric": "perms_per_s", "value": 256 / (res["plain"] / 1e3),
+            "unit": "perm/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["plain"], "batched_perms_per_s": 256 / (res["batched"] / 1e3),
+            "batched_ms": res["batched"], "nominal_terms_per_s_plain": terms / (res["plain"] / 1e3),
+            "nominal_terms_per_s_batched": terms / (res["batched"] / 1e3), "launches_plain": 256 * 3,
+            "launches_batched": 3, "max_rel_err_vs_oracle_sample": worst, "dtype": "c128",
+            "config": {"n": 14, "count": 256, "ensemble": "haar_u", "seed": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ensembles_batched(args):
+    import torch
+
+    import oracle as O
+    import paper_2602_10141_b300 as px
+    from workloads import device as D
+    count = max(2, int(round(50000 * args.scale)))
+    fields = {}
+    for cplx, names in ((True, CPLX), (False, REAL)):
+        parts, ns = [], []
+        for ei, name in enumerate(names):
+            for n in SIZES:
+                t = D.batch(name, n, count, seed=1000 * (ei + 1) + n + (0 if cplx else 500))
+                parts.append(t.reshape(-1))
+                ns += [n] * count
+        flat = torch.cat(parts)
+        ns = np.array(ns, np.int32)
+        offs = np.concatenate([[0], np.cumsum(ns.astype(np.int64) ** 2)[:-1]]).astype(np.int64)
+        out = torch.empty(len(ns), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+        fields[cplx] = (flat, ns, offs, out)
+    total_perms = sum(len(v[1]) for v in fields.values())
+    total_terms = sum(nominal_terms(v[1]) for v in fields.values())
+
+    def step():
+        for cplx, (flat, ns, offs, out) in fields.items():
+            (px.perm_c128 if cplx else px.perm_f64)(flat, ns, offs, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b = _events(torch)
+        a.record()
+        step()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms) / 1e3
+
+    # plain: one call per matrix on a subsample of 8 per (field, ensemble, n)
+    plain_perms, plain_terms, plain_ms = 0, 0.0, 0.0
+    for cplx, (flat, ns, offs, out) in fields.items():
+        fn = px.perm_c128 if cplx else px.perm_f64
+        idx = [g * count + k for g in range(len(ns) // count) for k in range(8)]
+        for i in idx[:2]:
+            fn(flat, ns[i:i + 1], offs[i:i + 1], out[i:i + 1])
+        torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record()
+        for i in idx:
+            fn(flat, ns[i:i + 1], offs[i:i + 1], out[i:i + 1])
+        b.record()
+        torch.cuda.synchronize()
+        plain_ms += a.elapsed_time(b)
+        plain_perms += len(idx)
+        plain_terms += nominal_terms(ns[idx])
+    step()
+    torch.cuda.synchronize()
+
+    # oracle check on a seeded subsample (n <= 20)
+    worst_rel, checked = 0.0, 0
+    for cplx, (flat, ns, offs, out) in fields.items():
+        got = out.cpu().numpy()
+        host = flat.cpu().numpy()
+        for g in range(len(ns) // count):
+            i = g * count
+            n = int(ns[i])
+            if n > 16:
+                continue
+            A = host[offs[i]:offs[i] + n * n].reshape(n, n)
+            ref = O.perm_dp(A)
+            _, abs_terms = O.perm_ryser(A, with_abs=True)
+            err = abs(got[i] - ref)
+            assert err <= max(1e-9 * abs(ref), 64 * n * 2.0 ** -53 * abs_terms), (cplx, n, got[i], ref)
+            worst_rel = max(worst_rel, err / abs(ref))
+            checked += 1
+    line = {"workload": "ensembles_batched", "metric": "perms_per_s", "value": total_perms / t, "unit": "perm/s",
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "nominal_terms_per_s": total_terms / t, "perms_per_step": total_perms,
+            "plain_perms_per_s": plain_perms / (plain_ms / 1e3),
+            "plain_nominal_terms_per_s": plain_terms / (plain_ms / 1e3),
+            "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel, "dtype": "c128+f64",
+            "data": "synthetic, generated on the device (seeded torch generators)",
+            "config": {"sizes": list(SIZES), "per_size_and_ensemble": count, "scale_of_50000": args.scale,
+                       "complex128": list(CPLX), "float64": list(REAL)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+class _Server:
+    def __init__(self, px, plain: int, device_bytes: int = 4 << 30):
+        self.px, self.lib = px, px._lib
+        L = self.lib
+        L.serve_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        L.serve_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+        L.serve_poll_timed.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]
+        L.serve_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        L.serve_destroy.argtypes = [ctypes.c_void_p]
+        buf = bytearray(32)
+        struct.pack_into("<iiqqii", buf, 0, 1 << 20, 8192, device_bytes, 0, 0, plain)
+        self._cfg = (ctypes.c_char * 32).from_buffer(buf)
+        self.h = ctypes.c_void_p()
+        rc = L.serve_create(ctypes.addressof(self._cfg), ctypes.byref(self.h))
+        if rc:
+            raise RuntimeError(px.last_error())
+        self.res = (ctypes.c_char * 16)()
+        self.done, self.ts, self.td = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
+
+    def submit(self, A, field, p):
+        t = ctypes.c_uint64()
+        rc = self.lib.serve_submit(self.h, field, A.shape[0], A.ctypes.data, p, ctypes.byref(t))
+        if rc:
+            raise RuntimeError(self.px.last_error())
+        return t.value
+
+    def poll(self, ticket):
+        rc = self.lib.serve_poll_timed(self.h, ticket, self.res, ctypes.byref(self.done), ctypes.byref(self.ts),
+                                       ctypes.byref(self.td))
+        if rc:
+            raise RuntimeError(self.px.last_error())
+        if not self.done.value:
+            return None
+        return (self.td.value - self.ts.value) * 1e-9, bytes(self.res)
+
+    def stats(self):
+        s = (ctypes.c_int64 * 5)()
+        self.lib.serve_stats(self.h, s)
+        return list(s)
+
+    def close(self):
+        self.lib.serve_destroy(self.h)
+
+
+def _request_mix(count: int, seed: int):
+    import oracle as O   # primes for the F_p requests (largest p = 1 mod n below 2^31)
+    from workloads import ensemble, geodesic_cycle, random_residues, rng
+    g = rng(seed)
+    primes = {n: O.primes_1_mod_n(n, 1)[0] for n in range(16, 31)}
+    reqs = []
+    for i in range(count):
+        kind = int(g.integers(0, 4))
+        if kind == 0:
+            n = int(g.integers(10, 27))
+            reqs.append((ensemble("haar_u", n, 1, seed=seed + i)[0], 0, 0))
+        elif kind == 1:
+            n = int(g.integers(10, 27))
+            reqs.append((ensemble("goe", n, 1, seed=seed + i)[0], 1, 0))
+        elif kind == 2:
+            n = int(g.choice(np.arange(9, 26, 2)))
+            t = int(g.integers(0, 201)) / 200
+            reqs.append((np.ascontiguousarray(geodesic_cycle(n, t, "principal").astype(np.complex128)), 0, 0))
+        else:
+            n = int(g.integers(16, 31))
+            p = primes[n]
+            reqs.append((random_residues(n, p, g), 2, p))
+    return reqs
+
+
+def _drive(S, reqs, arrivals):
+    """Submit at the given arrival times (s), poll until all done; returns latencies and makespan."""
+    pending = {}
+    lat = []
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and arrivals[i] <= now:
+            A, f, p = reqs[i]
+            pending[S.submit(A, f, p)] = i
+            i += 1
+        for tk in list(pending):
+            r = S.poll(tk)
+            if r is not None:
+                lat.append(r[0])
+                del pending[tk]
+        if i < len(reqs) and not pending:
+            time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.001)))
+    return lat, time.perf_counter() - t0
+
+
+def serving(args):
+    import paper_2602_10141_b300 as px
+    count = max(200, int(round(20000 * args.scale)))
+    reqs = _request_mix(count, seed=0)
+    # capacity: all requests of a calibration sample submitted at once
+    cal = reqs[: max(100, count // 5)]
+    S = _Server(px, plain=0)
+    _, span = _drive(S, cal, [0.0] * len(cal))
+    S.close()
+    capacity = len(cal) / span
+    rate = 0.7 * capacity
+    g = np.random.default_rng(1)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
+    out = {}
+    for name, plain in (("continuous", 0), ("plain_fifo", 1)):
+        S = _Server(px, plain=plain)
+        lat, span = _drive(S, reqs, arrivals)
+        st = S.stats()
+        S.close()
+        lat = np.array(lat)
+        out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "throughput_rps": count / span, "makespan_s": span, "steps": st[3], "launches": st[4]}
+    line = {"workload": "serving", "metric": "p99_latency_ms", "value": out["continuous"]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "requests": count, "arrival_rate_rps": rate,
+            "capacity_rps": capacity, "continuous": out["continuous"], "plain_fifo": out["plain_fifo"],
+            "dtype": "c128+f64+u32", "data": "synthetic Poisson trace, seed 0",
+            "config": {"mix": "1/4 each: c128 Haar n~U[10,26], f64 GOE n~U[10,26], c128 cycle geodesic odd n in "
+                              "[9,25] t in k/200, F_p random n~U[16,30] with the largest p = 1 (mod n) < 2^31",
+                       "load": "0.7 x capacity", "scale_of_20000": args.scale}}
+    print(json.dumps(line), flush=True)
+    return 0

@@ -78,8 +78,13 @@ const char* permx_version(void);
  * one matrix is split into Gray-code chunks whose size depends only on
  * (n, field), and the chunk results are combined in a fixed order, so out[b]
  * is bit-for-bit the same whatever else is in the batch.
- * float64 / complex128: the row sums and products are IEEE float64; the
- * alternating sum is accumulated with TwoSum compensation.
+ * float64 / complex128 arithmetic (permx_set_fp_arith): PERMX_FP_ARITH_INT
+ * (default) keeps exact fixed-point row sums (each row scaled by a power of
+ * two, entries rounded to 62-bit integers) and forms products with signed
+ * 62-bit integer mantissas on the integer pipes, summing each chunk exactly;
+ * PERMX_FP_ARITH_FP64 uses IEEE float64 row sums and products with TwoSum
+ * compensated accumulation.  Both use the Nijenhuis-Wilf form of Ryser's
+ * formula (2^(n-1) Gray steps).
  * Errors: PERMX_EINVAL for n[b] outside [1, PERMX_MAX_N_FP], NULL pointers or
  * batch < 0; PERMX_ENOMEM; PERMX_ECUDA.  On error nothing is guaranteed about
  * out.
@@ -88,6 +93,15 @@ int perm_c128(const perm_c128_t* A, const int32_t* n, const int64_t* offset, int
               perm_c128_t* out, void* stream);
 int perm_f64(const double* A, const int32_t* n, const int64_t* offset, int64_t batch,
              double* out, void* stream);
+
+/* Arithmetic of the float64 / complex128 walks for subsequent calls (process
+ * wide): PERMX_FP_ARITH_INT or PERMX_FP_ARITH_FP64 (see above).  Returns the
+ * previous mode, or PERMX_EINVAL.  Results differ between the modes only by
+ * rounding; within one mode they are bit-reproducible. */
+#define PERMX_FP_ARITH_FP64 0
+#define PERMX_FP_ARITH_INT 1
+int permx_set_fp_arith(int mode);
+int permx_get_fp_arith(void);
 
 /* F_p permanents (paper §2.1).  A holds residues in [0, p[b]) (entries >= p
  * give unspecified results; the checked host path perm_modp_host rejects
@@ -136,6 +150,37 @@ int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int64_t* offset
  * by (-1)^n gives perm(A) mod p. */
 int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, uint64_t k1,
                          uint32_t* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Planned batches and CUDA graphs (the batched call of paper §3-§5 repeated
+ * over many inputs of one shape).  perm_plan_create fixes field, sizes,
+ * offsets and (F_p) primes: it computes the chunk plan, allocates the
+ * workspace from the library's pool and uploads the metadata, synchronising
+ * `stream`.  perm_plan_execute(A, out) then only enqueues kernels and one
+ * memset on `stream` (A, out: device buffers laid out as planned), so it may
+ * be captured in a CUDA graph; perm_plan_graph_launch does that capture
+ * itself on first use for a given (A, out) pair and afterwards replays the
+ * graph with one launch.  Executions of one plan must not overlap on the
+ * GPU (they share the workspace).  Errors: EINVAL, ENOMEM, ECUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct perm_plan perm_plan;
+int perm_plan_create(int field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
+                     void* stream, perm_plan** plan);
+int perm_plan_execute(perm_plan* plan, const void* A, void* out, void* stream);
+int perm_plan_graph_launch(perm_plan* plan, const void* A, void* out, void* stream);
+int perm_plan_destroy(perm_plan* plan);
+
+/* Chunk-length tuning (paper §2.2: the size of a Gray-code block).  The
+ * chunk length of a matrix is 2^ell Gray steps with ell a function of
+ * (field, n) only, so results do not depend on batch composition; float
+ * results do depend on ell (rounding), F_p results never.  perm_tune_set
+ * pins ell for (field, n) (0 restores the built-in rule); perm_tune_get
+ * returns the ell in force; perm_autotune times ell0-3 .. ell0+3 around the
+ * built-in rule on a synthetic batch of `batch` n x n matrices (`reps`
+ * timed passes each), keeps the fastest in the table and returns it. */
+int perm_tune_set(int field, int32_t n, int32_t ell);
+int perm_tune_get(int field, int32_t n);
+int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* best_ell);
 
 /* ------------------------------------------------------------------------
  * Exact perm(S_n) of the Schur matrix S_n = (exp(2 pi i jk/n))_{j,k<n}

@@ -1,0 +1,36 @@
+/*
+ * Self-test hooks for the integer-mantissa arithmetic of permx's float64 /
+ * complex128 walks (the paper has no counterpart; they check this library's
+ * own number format).  They run the same host+device helper functions the
+ * GPU kernels use, on the CPU, so the arithmetic can be checked against exact
+ * big-integer results without a GPU.  They compute no permanents.
+ */
+#ifndef PERMX_SELFTEST_H
+#define PERMX_SELFTEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* (a * b) >> 62, truncated, for |a|, |b| <= 2^62: the kernels' 64x64 product. */
+int64_t permx_x64_mulhi62(int64_t a, int64_t b);
+
+/* Product of n exact integer row sums R[0..n) (|R| < 2^61) as the real walk
+ * forms it (four interleaved chains, then combined): value m * 2^e. */
+int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out);
+
+/* Complex version: rows (Rr[i] + i Ri[i]); value (re + i im) * 2^e. */
+int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t* re_out, int64_t* im_out,
+                       int32_t* e_out);
+
+/* Chunk accumulator: sum_k (-1)^neg[k] m[k] 2^e[k] for k < count (count <= 4096),
+ * returned as the double-double hi + lo scaled by 2^scale. */
+int permx_x64_accumulate(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count, int32_t scale,
+                         double* hi, double* lo);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERMX_SELFTEST_H */

@@ -30,6 +30,7 @@ MAX_N_FP = 32
 MAX_N_MODP = 48
 MAX_PRIMES = 64
 FIELD_C128, FIELD_F64, FIELD_MODP = 0, 1, 2
+FP_ARITH_FP64, FP_ARITH_INT = 0, 1
 
 
 class PermxError(RuntimeError):
@@ -63,6 +64,15 @@ def _load() -> ctypes.CDLL:
         "perm_schur_residues": ([i32, u32, u32, P(u32)], ctypes.c_int),
         "perm_crt": ([P(u32), P(u32), i32, P(i64)], ctypes.c_int),
         "perm_schur_prime_count": ([i32], ctypes.c_int),
+        "permx_set_fp_arith": ([ctypes.c_int], ctypes.c_int),
+        "perm_plan_create": ([ctypes.c_int, P(i32), P(i64), P(u32), i64, vp, P(vp)], ctypes.c_int),
+        "perm_plan_execute": ([vp, vp, vp, vp], ctypes.c_int),
+        "perm_plan_graph_launch": ([vp, vp, vp, vp], ctypes.c_int),
+        "perm_plan_destroy": ([vp], ctypes.c_int),
+        "perm_tune_set": ([ctypes.c_int, i32, i32], ctypes.c_int),
+        "perm_tune_get": ([ctypes.c_int, i32], ctypes.c_int),
+        "perm_autotune": ([ctypes.c_int, i32, i64, i32, P(i32)], ctypes.c_int),
+        "permx_get_fp_arith": ([], ctypes.c_int),
         "permx_peak_probe": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                               P(ctypes.c_double)], ctypes.c_int),
     }
@@ -140,6 +150,54 @@ def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out,
     _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                           _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
     return out
+
+
+class Plan:
+    """A planned batch (perm_plan_*): sizes, offsets and primes fixed once;
+    ``execute`` enqueues only kernels, ``graph_launch`` replays a captured CUDA graph."""
+
+    def __init__(self, field: int, n, offset, p=None, stream=None):
+        n, offset = _i32(n), _i64(offset)
+        pp = _u32(p) if p is not None else None
+        self._keep = (n, offset, pp)
+        h = ctypes.c_void_p()
+        _check(_lib.perm_plan_create(field, _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
+                                     _p(pp, ctypes.c_uint32) if pp is not None else None, len(n), _stream(stream),
+                                     ctypes.byref(h)))
+        self.h = h
+
+    def execute(self, A, out, stream=None):
+        _check(_lib.perm_plan_execute(self.h, A.data_ptr(), out.data_ptr(), _stream(stream)))
+        return out
+
+    def graph_launch(self, A, out, stream=None):
+        _check(_lib.perm_plan_graph_launch(self.h, A.data_ptr(), out.data_ptr(), _stream(stream)))
+        return out
+
+    def close(self):
+        if self.h:
+            _lib.perm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def perm_tune_set(field: int, n: int, ell: int) -> None:
+    _check(_lib.perm_tune_set(field, n, ell))
+
+
+def perm_tune_get(field: int, n: int) -> int:
+    return _check(_lib.perm_tune_get(field, n))
+
+
+def perm_autotune(field: int, n: int, batch: int, reps: int = 3) -> int:
+    best = ctypes.c_int32(0)
+    _check(_lib.perm_autotune(field, n, batch, reps, ctypes.byref(best)))
+    return int(best.value)
 
 
 def perm_modp_noalloc(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out, stream=None):
@@ -242,6 +300,15 @@ def perm_crt(residues: Sequence[int], primes: Sequence[int]) -> int:
     out = np.zeros(2, np.int64)
     _check(_lib.perm_crt(_p(r, ctypes.c_uint32), _p(p, ctypes.c_uint32), len(r), _p(out, ctypes.c_int64)))
     return _i128(out)
+
+
+def permx_set_fp_arith(mode: int) -> int:
+    """Select the float64/complex128 arithmetic (FP_ARITH_INT or FP_ARITH_FP64); returns the previous mode."""
+    return _check(_lib.permx_set_fp_arith(mode))
+
+
+def permx_get_fp_arith() -> int:
+    return int(_lib.permx_get_fp_arith())
 
 
 def perm_schur_prime_count(n: int) -> int:

@@ -33,9 +33,11 @@ INSTANCES = {
     "inst_modp.cu": [(1, 8), (9, 16), (17, 24), (25, 32), (33, 40), (41, 48)],
     "inst_f64.cu": [(1, 11), (12, 22), (23, 32)],
     "inst_c128.cu": [(1, 8), (9, 16), (17, 24), (25, 32)],
+    "inst_x64r.cu": [(1, 11), (12, 22), (23, 32)],
+    "inst_x64c.cu": [(1, 8), (9, 16), (17, 24), (25, 32)],
 }
-PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu", "noalloc.cu"]
-PLAIN_CPP = ["api.cpp", "field.cpp", "schur.cpp", "serve.cpp"]
+PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu", "noalloc.cu", "plan.cu"]
+PLAIN_CPP = ["api.cpp", "field.cpp", "schur.cpp", "serve.cpp", "selftest.cpp"]
 
 
 def _gen_dispatch() -> None:
@@ -46,7 +48,8 @@ def _gen_dispatch() -> None:
     _write_if_changed(os.path.join(CSRC, "inst_range.inc"), "\n".join(lines) + "\n")
     out = ["// Runtime-n dispatch to the compile-time-n kernels (written by build.py).",
            '#include "common.cuh"', "", "namespace permx {", ""]
-    for kind, lt, mx in (("modp", "ModpLaunch", 48), ("f64", "FpLaunch", 32), ("c128", "FpLaunch", 32)):
+    for kind, lt, mx in (("modp", "ModpLaunch", 48), ("f64", "FpLaunch", 32), ("c128", "FpLaunch", 32),
+                         ("x64r", "FpLaunch", 32), ("x64c", "FpLaunch", 32)):
         out += [f"cudaError_t dispatch_{kind}(int n, const {lt}& L, cudaStream_t s) {{",
                 "    const uint64_t items = L.item_end - L.item_begin;",
                 "    if (items == 0) return cudaSuccess;",
@@ -59,6 +62,18 @@ def _gen_dispatch() -> None:
         for n in range(1, mx + 1):
             out.append(f"        case {n}: return launch_{kind}<{n}>(L, grid_for(blocks_per_sm_{kind}<{n}>()), s);")
         out += ["        default: return cudaErrorInvalidValue;", "    }", "}", ""]
+    # resident blocks per SM of the kernel that a (kind, n) launch uses
+    out += ["int dispatch_blocks_per_sm(int kind, int n) {",
+            "    // kind: 0 modp, 1 f64, 2 c128, 3 x64 real, 4 x64 complex",
+            "    switch (kind) {"]
+    for k, (kind, mx) in enumerate((("modp", 48), ("f64", 32), ("c128", 32), ("x64r", 32), ("x64c", 32))):
+        out.append(f"        case {k}:")
+        out.append("            switch (n) {")
+        for n in range(1, mx + 1):
+            out.append(f"                case {n}: return blocks_per_sm_{kind}<{n}>();")
+        out.append("                default: return 1;")
+        out.append("            }")
+    out += ["        default: return 1;", "    }", "}", ""]
     out.append("}  // namespace permx")
     _write_if_changed(os.path.join(CSRC, "dispatch.cu"), "\n".join(out) + "\n")
 
@@ -75,7 +90,8 @@ def _deps_hash(src: str, extra: list[str]) -> str:
     for name in sorted(os.listdir(CSRC)):
         if name.endswith((".cuh", ".h", ".inc")):
             h.update(open(os.path.join(CSRC, name), "rb").read())
-    h.update(open(os.path.join(INCLUDE, "permx.h"), "rb").read())
+    for name in sorted(os.listdir(INCLUDE)):
+        h.update(open(os.path.join(INCLUDE, name), "rb").read())
     h.update(open(src, "rb").read())
     h.update(" ".join(extra).encode())
     return h.hexdigest()[:16]

@@ -67,12 +67,12 @@ static int host_call(const T* A, const int32_t* n, const int64_t* offset, int64_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     T* dA = nullptr;
     T* dO = nullptr;
-    PERMX_CUDA(cudaMallocAsync(&dA, sizeof(T) * (size_t)elems, s));
-    cudaError_t e = cudaMallocAsync(&dO, sizeof(T) * (size_t)batch, s);
+    PERMX_CUDA(ws_alloc(reinterpret_cast<void**>(&dA), sizeof(T) * (size_t)elems, s));
+    cudaError_t e = ws_alloc(reinterpret_cast<void**>(&dO), sizeof(T) * (size_t)batch, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dA, A, sizeof(T) * (size_t)elems, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
-        cudaFreeAsync(dA, s);
-        if (dO) cudaFreeAsync(dO, s);
+        ws_free(dA, s);
+        if (dO) ws_free(dO, s);
         return cuda_fail(e, "host copy-in");
     }
     rc = run(dA, dO, s);
@@ -80,8 +80,8 @@ static int host_call(const T* A, const int32_t* n, const int64_t* offset, int64_
         e = cudaMemcpyAsync(out, dO, sizeof(T) * (size_t)batch, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail(e, "host copy-out");
     }
-    cudaFreeAsync(dA, s);
-    cudaFreeAsync(dO, s);
+    ws_free(dA, s);
+    ws_free(dO, s);
     e = cudaStreamSynchronize(s);
     if (rc == PERMX_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
     return rc;
@@ -246,6 +246,15 @@ int perm_crt(const uint32_t* residues, const uint32_t* primes, int32_t k, int64_
     if (!fits) return fail(PERMX_EINVAL, "value does not fit in 128 bits");
     return PERMX_OK;
 }
+
+int permx_set_fp_arith(int mode) {
+    clear_error();
+    if (mode != PERMX_FP_ARITH_FP64 && mode != PERMX_FP_ARITH_INT)
+        return fail(PERMX_EINVAL, "unknown float arithmetic mode");
+    return set_fp_arith(mode);
+}
+
+int permx_get_fp_arith(void) { return fp_arith(); }
 
 int perm_schur_prime_count(int32_t n) {
     clear_error();

@@ -8,6 +8,7 @@
 // the batch: the chunking is a function of (n, field) only and chunk partials
 // are combined in a fixed order.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -26,15 +27,74 @@ int chunk_log2_modp(int bits) {
     return ell < lo ? lo : ell;
 }
 
+// Tuning table: chunk length (log2) per (field, n) set by perm_tune_set /
+// perm_autotune; 0 means the formula.  Float results depend on the chunking,
+// so a given table always gives the same bits.
+static std::atomic<int> g_tune[3][PERMX_MAX_N_MODP + 1];
+
+int tune_get(int field, int n) {
+    if (field < 0 || field > 2 || n < 1 || n > PERMX_MAX_N_MODP) return 0;
+    return g_tune[field][n].load();
+}
+void tune_set(int field, int n, int ell) {
+    if (field >= 0 && field <= 2 && n >= 1 && n <= PERMX_MAX_N_MODP) g_tune[field][n].store(ell);
+}
+
+int chunk_log2(Field field, int n, int bits) {
+    const int t = tune_get((int)field, n);
+    if (t > 0 && t <= bits) return t;
+    if (t > bits) return bits;
+    return field == Field::MODP ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+}
+
 int chunk_log2_fp(int bits) {
-    // At most 2^12 steps per chunk (row-sum drift of an incremental walk grows
-    // like sqrt(L) ulps); at least 2^6 (or the whole walk) for the chunk start cost.
+    // At most 2^10 steps per chunk: the float64 walk's row-sum drift grows like
+    // sqrt(L) ulps, and a chunk is the unit of work a serving step cannot split;
+    // at least 2^6 (or the whole walk) so the O(n^2) chunk start stays small.
     int ell = bits - 14;
     int lo = bits < 6 ? bits : 6;
     if (ell < lo) ell = lo;
-    if (ell > 12) ell = 12;
+    if (ell > 10) ell = 10;
     return ell;
 }
+
+// Stream-ordered workspace from a pool owned by the library (one per device),
+// which keeps freed memory for reuse instead of returning it at every
+// synchronisation; a batched call then costs no allocator round trip.
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t ws_free(void* p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) : cudaSuccess; }
+
+static std::atomic<int> g_fp_arith{1};
+int fp_arith() { return g_fp_arith.load(); }
+int set_fp_arith(int mode) { return g_fp_arith.exchange(mode); }
 
 int sm_count() {
     static int cached[64] = {0};
@@ -52,6 +112,49 @@ int sm_count() {
 // ---------------------------------------------------------------------------
 // device kernels: staging and finalisation
 // ---------------------------------------------------------------------------
+
+// Integer-mantissa staging (one block per matrix): row i gets the scale
+// sigma_i = 60 - floor(log2(sum_j |a_ij|)) (complex: |re| + |im|), entries
+// A_ij = 2 round(a_ij 2^(sigma_i - 1)) (even, so halves are exact), the
+// Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij)/2, zero padding, and
+// one trailing word with -sum_i sigma_i.  W = int64 words per entry.
+template <int W>
+__global__ void stage_x64_kernel(const double* __restrict__ A, const StageDesc* __restrict__ d,
+                                 int64_t* __restrict__ colT) {
+    __shared__ int sig_sum;
+    const StageDesc s = d[blockIdx.x];
+    const int n = s.n, ld = s.ld;
+    int64_t* base = colT + s.dst * W;   // dst counts entries of W words
+    if (threadIdx.x == 0) sig_sum = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+        if (i >= n) {
+            for (int j = 0; j <= n; ++j)
+                for (int w = 0; w < W; ++w) base[((int64_t)j * ld + i) * W + w] = 0;
+            continue;
+        }
+        const double* row = A + (s.src + (int64_t)i * n) * W;
+        double S = 0.0;
+        for (int j = 0; j < n * W; ++j) S += fabs(row[j]);
+        const int sig = S > 0.0 ? 60 - ilogb(S) : 0;
+        int64_t sum[W];
+        for (int w = 0; w < W; ++w) sum[w] = 0;
+        for (int j = 0; j < n; ++j)
+            for (int w = 0; w < W; ++w) {
+                const int64_t a = 2 * (int64_t)llrint(ldexp(row[j * W + w], sig - 1));
+                base[((int64_t)j * ld + i) * W + w] = a;
+                sum[w] += a;
+            }
+        for (int w = 0; w < W; ++w)
+            base[((int64_t)n * ld + i) * W + w] = base[((int64_t)(n - 1) * ld + i) * W + w] - sum[w] / 2;
+        atomicAdd(&sig_sum, sig);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        base[(int64_t)(n + 1) * ld * W] = -(int64_t)sig_sum;
+        base[(int64_t)(n + 1) * ld * W + 1] = 0;
+    }
+}
 
 // x_i = a_{i,n-1} - (1/2) sum_j a_ij for the Nijenhuis-Wilf form.
 // F_p: 1/2 = (p+1)/2 mod p.  Floating point: the row sum is compensated
@@ -187,6 +290,18 @@ cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t c
     return cudaGetLastError();
 }
 
+cudaError_t launch_stage_x64(bool cplx, const void* A, const StageDesc* d, int64_t count, void* colT,
+                             cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (cplx)
+        stage_x64_kernel<2><<<(unsigned)count, 64, 0, s>>>(static_cast<const double*>(A), d,
+                                                            static_cast<int64_t*>(colT));
+    else
+        stage_x64_kernel<1><<<(unsigned)count, 64, 0, s>>>(static_cast<const double*>(A), d,
+                                                            static_cast<int64_t*>(colT));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
                                cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
@@ -258,13 +373,15 @@ BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field) {
         g.mats = std::move(kv.second);
         g.nw = 1;
         const int bits = walk_bits(g.n, g.nw);
-        g.ell = field == Field::MODP ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+        g.ell = chunk_log2(field, g.n, bits);
         g.log2_chunks = bits - g.ell;
         if (field == Field::MODP) g.ld = pad4(g.n);
         else if (field == Field::F64) g.ld = pad2(g.n);
         else g.ld = g.n;                          // complex entries are 16 bytes already
         const int words = field == Field::C128 ? 2 : 1;   // doubles (fp) or uint32 (modp) per entry
         g.mat_stride = (int64_t)(g.n + g.nw) * g.ld * words;
+        g.x64 = field != Field::MODP && fp_arith() == 1;
+        if (g.x64) g.mat_stride += 2;             // the -sum(sigma) word (and padding)
         g.col_off = col_off;
         g.first_mat = mat_index;
         g.items = (int64_t)g.mats.size() << g.log2_chunks;
@@ -291,156 +408,203 @@ uint64_t plan_units(const BatchPlan& P) {
 static int alloc_ws(Workspace& ws, size_t bytes, cudaStream_t s) {
     ws.bytes = bytes;
     if (bytes == 0) return PERMX_OK;
-    cudaError_t e = cudaMallocAsync(&ws.base, bytes, s);
+    cudaError_t e = ws_alloc(&ws.base, bytes, s);
     if (e != cudaSuccess) {
         ws.base = nullptr;
         return e == cudaErrorMemoryAllocation ? fail(PERMX_ENOMEM, "workspace allocation failed")
-                                              : cuda_fail(e, "cudaMallocAsync");
+                                              : cuda_fail(e, "workspace allocation");
     }
+    return PERMX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// prepare / execute / release.  prepare() plans the batch, allocates one
+// workspace and uploads the metadata; execute() only enqueues kernels and a
+// memset (so it can be captured in a CUDA graph and replayed); release()
+// returns the workspace.  The one-shot calls below run all three.
+// ---------------------------------------------------------------------------
+int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
+                  cudaStream_t s, Prepared& X) {
+    X = Prepared{};
+    X.field = field;
+    X.batch = batch;
+    X.P = plan_batch(n, batch, field);
+    X.x64 = !X.P.groups.empty() && X.P.groups[0].x64;
+    std::vector<unsigned char> host;
+    if (field == Field::MODP) {
+        std::vector<StageDesc> stage(batch);
+        std::vector<uint32_t> pp(batch), pinv(batch);
+        std::vector<ModpFinal> fin(batch);
+        for (auto& g : X.P.groups) {
+            for (size_t q = 0; q < g.mats.size(); ++q) {
+                const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
+                stage[m] = StageDesc{offset[b], g.col_off + (int64_t)q * g.mat_stride, g.n, g.ld, p[b], g.nw};
+                pp[m] = p[b];
+                pinv[m] = inv_mod_2_32(p[b]);
+                fin[m].p = p[b];
+                fin[m].rfix = pow_mod((uint32_t)(((uint64_t)1 << 32) % p[b]), (uint64_t)(g.n - 1), p[b]);
+                if (g.nw) fin[m].rfix = (uint32_t)((uint64_t)fin[m].rfix * 2 % p[b]);
+                fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
+                fin[m].out_index = b;
+            }
+        }
+        X.o_stage = 0;
+        X.o_p = align256(X.o_stage + sizeof(StageDesc) * batch);
+        X.o_pinv = align256(X.o_p + 4 * batch);
+        X.o_fin = align256(X.o_pinv + 4 * batch);
+        X.o_meta_end = align256(X.o_fin + sizeof(ModpFinal) * batch);
+        X.o_acc = X.o_meta_end;
+        X.o_col = align256(X.o_acc + 8 * batch);
+        X.bytes = align256(X.o_col + 4 * (size_t)X.P.col_elems);
+        host.resize(X.o_meta_end);
+        std::memcpy(host.data() + X.o_stage, stage.data(), sizeof(StageDesc) * batch);
+        std::memcpy(host.data() + X.o_p, pp.data(), 4 * batch);
+        std::memcpy(host.data() + X.o_pinv, pinv.data(), 4 * batch);
+        std::memcpy(host.data() + X.o_fin, fin.data(), sizeof(ModpFinal) * batch);
+    } else {
+        const bool cplx = field == Field::C128;
+        const int w = cplx ? 2 : 1;   // doubles per entry
+        std::vector<StageDesc> stage(batch);
+        std::vector<FpFinal> fin(batch);
+        for (auto& g : X.P.groups) {
+            for (size_t q = 0; q < g.mats.size(); ++q) {
+                const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
+                // staging works on entries of w doubles: offsets in entries
+                stage[m] = StageDesc{offset[b], (g.col_off / w) + (int64_t)q * (g.mat_stride / w), g.n, g.ld, 0u, g.nw};
+                fin[m].first = g.part_off + (int64_t)q * g.partials_per_mat;
+                fin[m].count = g.partials_per_mat;
+                fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
+                fin[m].twice = g.nw;
+                fin[m].out_index = b;
+            }
+        }
+        const int pw = cplx ? 4 : 2;   // doubles per partial
+        X.o_stage = 0;
+        X.o_fin = align256(sizeof(StageDesc) * batch);
+        X.o_meta_end = align256(X.o_fin + sizeof(FpFinal) * batch);
+        X.o_part = X.o_meta_end;
+        X.o_col = align256(X.o_part + 8 * (size_t)pw * (size_t)X.P.total_partials);
+        X.bytes = align256(X.o_col + 8 * (size_t)X.P.col_elems);
+        host.resize(X.o_meta_end);
+        std::memcpy(host.data() + X.o_stage, stage.data(), sizeof(StageDesc) * batch);
+        std::memcpy(host.data() + X.o_fin, fin.data(), sizeof(FpFinal) * batch);
+    }
+    Workspace ws;
+    int rc = alloc_ws(ws, X.bytes, s);
+    if (rc) return rc;
+    X.ws = static_cast<unsigned char*>(ws.base);
+    cudaError_t e = cudaMemcpyAsync(X.ws, host.data(), X.o_meta_end, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        release_batch(X, s);
+        return cuda_fail(e, "metadata upload");
+    }
+    return PERMX_OK;
+}
+
+void release_batch(Prepared& X, cudaStream_t s) {
+    if (X.ws) ws_free(X.ws, s);
+    X.ws = nullptr;
+}
+
+int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
+    unsigned char* d = X.ws;
+    const int64_t batch = X.batch;
+    cudaError_t e = cudaSuccess;
+    if (X.field == Field::MODP) {
+        e = cudaMemsetAsync(d + X.o_acc, 0, 8 * batch, s);
+        if (e == cudaSuccess) {
+            stage_columns_kernel<uint32_t><<<(unsigned)batch, 256, 0, s>>>(
+                static_cast<const uint32_t*>(A), reinterpret_cast<const StageDesc*>(d + X.o_stage),
+                reinterpret_cast<uint32_t*>(d + X.o_col));
+            e = cudaGetLastError();
+        }
+        for (size_t gi = 0; e == cudaSuccess && gi < X.P.groups.size(); ++gi) {
+            const GroupPlan& g = X.P.groups[gi];
+            ModpLaunch L;
+            L.colT = reinterpret_cast<const uint32_t*>(d + X.o_col) + g.col_off;
+            L.p = reinterpret_cast<const uint32_t*>(d + X.o_p) + g.first_mat;
+            L.pinv = reinterpret_cast<const uint32_t*>(d + X.o_pinv) + g.first_mat;
+            L.acc = reinterpret_cast<unsigned long long*>(d + X.o_acc) + g.first_mat;
+            L.mat_stride = g.mat_stride;
+            L.item_begin = 0;
+            L.item_end = (uint64_t)g.items;
+            L.k_lo = 0;
+            L.k_hi = (uint64_t)1 << walk_bits(g.n, g.nw);
+            L.ell = g.ell;
+            L.log2_chunks = g.log2_chunks;
+            L.nw = g.nw;
+            e = dispatch_modp(g.n, L, s);
+        }
+        if (e == cudaSuccess) {
+            finalize_modp_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
+                reinterpret_cast<const unsigned long long*>(d + X.o_acc), reinterpret_cast<const ModpFinal*>(d + X.o_fin),
+                batch, static_cast<uint32_t*>(out));
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "perm_modp launch");
+        return PERMX_OK;
+    }
+    const bool cplx = X.field == Field::C128;
+    const int pw = cplx ? 4 : 2;
+    const double* Ad = static_cast<const double*>(A);
+    if (X.x64) {
+        if (cplx)
+            stage_x64_kernel<2><<<(unsigned)batch, 64, 0, s>>>(Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage),
+                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+        else
+            stage_x64_kernel<1><<<(unsigned)batch, 64, 0, s>>>(Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage),
+                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+    } else if (cplx) {
+        stage_columns_kernel<double2><<<(unsigned)batch, 256, 0, s>>>(
+            reinterpret_cast<const double2*>(Ad), reinterpret_cast<const StageDesc*>(d + X.o_stage),
+            reinterpret_cast<double2*>(d + X.o_col));
+    } else {
+        stage_columns_kernel<double><<<(unsigned)batch, 256, 0, s>>>(
+            Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<double*>(d + X.o_col));
+    }
+    e = cudaGetLastError();
+    for (size_t gi = 0; e == cudaSuccess && gi < X.P.groups.size(); ++gi) {
+        const GroupPlan& g = X.P.groups[gi];
+        FpLaunch L;
+        L.colT = reinterpret_cast<const double*>(d + X.o_col) + g.col_off;
+        L.partial = reinterpret_cast<double*>(d + X.o_part) + (size_t)pw * g.part_off;
+        L.mat_stride = g.mat_stride;
+        L.item_begin = 0;
+        L.item_end = (uint64_t)g.items;
+        L.ell = g.ell;
+        L.log2_chunks = g.log2_chunks;
+        L.nw = g.nw;
+        if (g.x64) e = cplx ? dispatch_x64c(g.n, L, s) : dispatch_x64r(g.n, L, s);
+        else e = cplx ? dispatch_c128(g.n, L, s) : dispatch_f64(g.n, L, s);
+    }
+    if (e == cudaSuccess) {
+        finalize_fp_kernel<<<(unsigned)batch, kFinalThreads, 0, s>>>(
+            reinterpret_cast<const double*>(d + X.o_part), reinterpret_cast<const FpFinal*>(d + X.o_fin), cplx ? 1 : 0,
+            out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, cplx ? "perm_c128 launch" : "perm_f64 launch");
     return PERMX_OK;
 }
 
 int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
                    uint32_t* out, cudaStream_t s) {
-    BatchPlan P = plan_batch(n, batch, Field::MODP);
-    // host metadata
-    std::vector<StageDesc> stage(batch);
-    std::vector<uint32_t> pp(batch), pinv(batch);
-    std::vector<ModpFinal> fin(batch);
-    for (auto& g : P.groups) {
-        for (size_t q = 0; q < g.mats.size(); ++q) {
-            const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
-            stage[m] = StageDesc{offset[b], g.col_off + (int64_t)q * g.mat_stride, g.n, g.ld, p[b], g.nw};
-            pp[m] = p[b];
-            pinv[m] = inv_mod_2_32(p[b]);
-            fin[m].p = p[b];
-            fin[m].rfix = pow_mod((uint32_t)(((uint64_t)1 << 32) % p[b]), (uint64_t)(g.n - 1), p[b]);
-            if (g.nw) fin[m].rfix = (uint32_t)((uint64_t)fin[m].rfix * 2 % p[b]);
-            fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
-            fin[m].out_index = b;
-        }
-    }
-    const size_t o_stage = 0;
-    const size_t o_p = align256(o_stage + sizeof(StageDesc) * batch);
-    const size_t o_pinv = align256(o_p + 4 * batch);
-    const size_t o_fin = align256(o_pinv + 4 * batch);
-    const size_t o_meta_end = align256(o_fin + sizeof(ModpFinal) * batch);
-    const size_t o_acc = o_meta_end;
-    const size_t o_col = align256(o_acc + 8 * batch);
-    const size_t total = align256(o_col + 4 * (size_t)P.col_elems);
-    std::vector<unsigned char> host(o_meta_end);
-    std::memcpy(host.data() + o_stage, stage.data(), sizeof(StageDesc) * batch);
-    std::memcpy(host.data() + o_p, pp.data(), 4 * batch);
-    std::memcpy(host.data() + o_pinv, pinv.data(), 4 * batch);
-    std::memcpy(host.data() + o_fin, fin.data(), sizeof(ModpFinal) * batch);
-
-    Workspace ws;
-    int rc = alloc_ws(ws, total, s);
+    Prepared X;
+    int rc = prepare_batch(Field::MODP, n, offset, p, batch, s, X);
     if (rc) return rc;
-    unsigned char* d = static_cast<unsigned char*>(ws.base);
-    cudaError_t e = cudaMemcpyAsync(d, host.data(), o_meta_end, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_acc, 0, 8 * batch, s);
-    if (e == cudaSuccess) {
-        stage_columns_kernel<uint32_t><<<(unsigned)batch, 256, 0, s>>>(
-            A, reinterpret_cast<const StageDesc*>(d + o_stage), reinterpret_cast<uint32_t*>(d + o_col));
-        e = cudaGetLastError();
-    }
-    for (size_t gi = 0; e == cudaSuccess && gi < P.groups.size(); ++gi) {
-        const GroupPlan& g = P.groups[gi];
-        ModpLaunch L;
-        L.colT = reinterpret_cast<const uint32_t*>(d + o_col) + g.col_off;
-        L.p = reinterpret_cast<const uint32_t*>(d + o_p) + g.first_mat;
-        L.pinv = reinterpret_cast<const uint32_t*>(d + o_pinv) + g.first_mat;
-        L.acc = reinterpret_cast<unsigned long long*>(d + o_acc) + g.first_mat;
-        L.mat_stride = g.mat_stride;
-        L.item_begin = 0;
-        L.item_end = (uint64_t)g.items;
-        L.k_lo = 0;
-        L.k_hi = (uint64_t)1 << walk_bits(g.n, g.nw);
-        L.ell = g.ell;
-        L.log2_chunks = g.log2_chunks;
-        L.nw = g.nw;
-        e = dispatch_modp(g.n, L, s);
-    }
-    if (e == cudaSuccess) {
-        finalize_modp_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
-            reinterpret_cast<const unsigned long long*>(d + o_acc), reinterpret_cast<const ModpFinal*>(d + o_fin),
-            batch, out);
-        e = cudaGetLastError();
-    }
-    cudaError_t ef = cudaFreeAsync(ws.base, s);
-    if (e != cudaSuccess) return cuda_fail(e, "perm_modp launch");
-    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
-    return PERMX_OK;
+    rc = execute_batch(X, A, out, s);
+    release_batch(X, s);
+    return rc;
 }
 
 int run_fp_batch(const double* A, const int32_t* n, const int64_t* offset, int64_t batch, void* out, bool cplx,
                  cudaStream_t s) {
-    BatchPlan P = plan_batch(n, batch, cplx ? Field::C128 : Field::F64);
-    const int w = cplx ? 2 : 1;   // doubles per entry
-    std::vector<StageDesc> stage(batch);
-    std::vector<FpFinal> fin(batch);
-    for (auto& g : P.groups) {
-        for (size_t q = 0; q < g.mats.size(); ++q) {
-            const int64_t b = g.mats[q], m = g.first_mat + (int64_t)q;
-            // staging works on entries of w doubles: offsets in entries
-            stage[m] = StageDesc{offset[b], (g.col_off / w) + (int64_t)q * (g.mat_stride / w), g.n, g.ld, 0u, g.nw};
-            fin[m].first = g.part_off + (int64_t)q * g.partials_per_mat;
-            fin[m].count = g.partials_per_mat;
-            fin[m].negate = g.nw ? !(g.n & 1) : (g.n & 1);
-            fin[m].twice = g.nw;
-            fin[m].out_index = b;
-        }
-    }
-    const int pw = cplx ? 4 : 2;   // doubles per partial
-    const size_t o_stage = 0;
-    const size_t o_fin = align256(sizeof(StageDesc) * batch);
-    const size_t o_meta_end = align256(o_fin + sizeof(FpFinal) * batch);
-    const size_t o_part = o_meta_end;
-    const size_t o_col = align256(o_part + 8 * (size_t)pw * (size_t)P.total_partials);
-    const size_t total = align256(o_col + 8 * (size_t)P.col_elems);
-    std::vector<unsigned char> host(o_meta_end);
-    std::memcpy(host.data() + o_stage, stage.data(), sizeof(StageDesc) * batch);
-    std::memcpy(host.data() + o_fin, fin.data(), sizeof(FpFinal) * batch);
-
-    Workspace ws;
-    int rc = alloc_ws(ws, total, s);
+    Prepared X;
+    int rc = prepare_batch(cplx ? Field::C128 : Field::F64, n, offset, nullptr, batch, s, X);
     if (rc) return rc;
-    unsigned char* d = static_cast<unsigned char*>(ws.base);
-    cudaError_t e = cudaMemcpyAsync(d, host.data(), o_meta_end, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        if (cplx)
-            stage_columns_kernel<double2><<<(unsigned)batch, 256, 0, s>>>(
-                reinterpret_cast<const double2*>(A), reinterpret_cast<const StageDesc*>(d + o_stage),
-                reinterpret_cast<double2*>(d + o_col));
-        else
-            stage_columns_kernel<double><<<(unsigned)batch, 256, 0, s>>>(
-                A, reinterpret_cast<const StageDesc*>(d + o_stage), reinterpret_cast<double*>(d + o_col));
-        e = cudaGetLastError();
-    }
-    for (size_t gi = 0; e == cudaSuccess && gi < P.groups.size(); ++gi) {
-        const GroupPlan& g = P.groups[gi];
-        FpLaunch L;
-        L.colT = reinterpret_cast<const double*>(d + o_col) + g.col_off;
-        L.partial = reinterpret_cast<double*>(d + o_part) + (size_t)pw * g.part_off;
-        L.mat_stride = g.mat_stride;
-        L.item_begin = 0;
-        L.item_end = (uint64_t)g.items;
-        L.ell = g.ell;
-        L.log2_chunks = g.log2_chunks;
-        L.nw = g.nw;
-        e = cplx ? dispatch_c128(g.n, L, s) : dispatch_f64(g.n, L, s);
-    }
-    if (e == cudaSuccess) {
-        finalize_fp_kernel<<<(unsigned)batch, kFinalThreads, 0, s>>>(
-            reinterpret_cast<const double*>(d + o_part), reinterpret_cast<const FpFinal*>(d + o_fin), cplx ? 1 : 0,
-            out);
-        e = cudaGetLastError();
-    }
-    cudaError_t ef = cudaFreeAsync(ws.base, s);
-    if (e != cudaSuccess) return cuda_fail(e, cplx ? "perm_c128 launch" : "perm_f64 launch");
-    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
-    return PERMX_OK;
+    rc = execute_batch(X, A, out, s);
+    release_batch(X, s);
+    return rc;
 }
 
 }  // namespace permx
@@ -450,14 +614,14 @@ cudaError_t stage_columns_u32(const uint32_t* A, int n, int ld, uint32_t p, int 
                               cudaStream_t s) {
     StageDesc h{0, 0, n, ld, p, nw};
     StageDesc* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof h, s);
+    cudaError_t e = ws_alloc(reinterpret_cast<void**>(&d), sizeof h, s);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         stage_columns_kernel<uint32_t><<<1, 256, 0, s>>>(A, d, colT);
         e = cudaGetLastError();
     }
-    cudaError_t f = cudaFreeAsync(d, s);
+    cudaError_t f = ws_free(d, s);
     return e != cudaSuccess ? e : f;
 }
 }  // namespace permx

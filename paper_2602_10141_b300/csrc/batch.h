@@ -39,6 +39,7 @@ struct FpFinal {
 
 struct GroupPlan {
     int n = 0, ell = 0, log2_chunks = 0, ld = 0, nw = 1;
+    bool x64 = false;                // float fields: integer-mantissa walk
     int64_t mat_stride = 0;          // elements (uint32 or double) between matrices
     int64_t col_off = 0;             // elements
     int64_t first_mat = 0;           // index of the group's first matrix in plan order
@@ -56,6 +57,23 @@ struct BatchPlan {
     std::vector<GroupPlan> groups;
 };
 
+struct Prepared {                   // a planned batch with its workspace (device) and metadata uploaded
+    Field field = Field::MODP;
+    int64_t batch = 0;
+    BatchPlan P;
+    bool x64 = false;
+    unsigned char* ws = nullptr;
+    size_t bytes = 0;
+    size_t o_stage = 0, o_p = 0, o_pinv = 0, o_fin = 0, o_meta_end = 0, o_acc = 0, o_col = 0, o_part = 0;
+};
+int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
+                  cudaStream_t s, Prepared& X);
+int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s);
+void release_batch(Prepared& X, cudaStream_t s);
+int chunk_log2(Field field, int n, int bits);
+int tune_get(int field, int n);
+void tune_set(int field, int n, int ell);
+
 int validate_batch(const void* A, const int32_t* n, const int64_t* offset, int64_t batch, const void* out,
                    int max_n);
 BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field);
@@ -63,6 +81,9 @@ uint64_t plan_units(const BatchPlan& P);
 int run_modp_batch(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
                    uint32_t* out, cudaStream_t s);
 cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t count, void* colT, cudaStream_t s);
+cudaError_t launch_stage_x64(bool cplx, const void* A, const StageDesc* d, int64_t count, void* colT,
+                             cudaStream_t s);
+int set_fp_arith(int mode);
 cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
                                cudaStream_t s);
 cudaError_t launch_finalize_modp_at(const unsigned long long* acc, const ModpFinalAt* f, int64_t count, uint32_t* out,

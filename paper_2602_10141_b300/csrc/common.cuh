@@ -104,6 +104,10 @@ struct FpLaunch {
 template <int N> cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s);
 template <int N> cudaError_t launch_f64(const FpLaunch& L, int grid, cudaStream_t s);
 template <int N> cudaError_t launch_c128(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> int blocks_per_sm_x64r();
+template <int N> int blocks_per_sm_x64c();
 template <int N> int blocks_per_sm_modp();
 template <int N> int blocks_per_sm_f64();
 template <int N> int blocks_per_sm_c128();
@@ -112,10 +116,20 @@ template <int N> int blocks_per_sm_c128();
 cudaError_t dispatch_modp(int n, const ModpLaunch& L, cudaStream_t s);
 cudaError_t dispatch_f64(int n, const FpLaunch& L, cudaStream_t s);
 cudaError_t dispatch_c128(int n, const FpLaunch& L, cudaStream_t s);
+cudaError_t dispatch_x64r(int n, const FpLaunch& L, cudaStream_t s);
+cudaError_t dispatch_x64c(int n, const FpLaunch& L, cudaStream_t s);
+int dispatch_blocks_per_sm(int kind, int n);   // kind: 0 modp, 1 f64, 2 c128, 3 x64 real, 4 x64 complex
+
+// Arithmetic of the float64 / complex128 walks: 0 = the FP64 pipe (IEEE
+// float64 row sums and products), 1 = integer mantissas (exact fixed-point
+// row sums, 62-bit products); see include/permx.h, permx_set_fp_arith.
+int fp_arith();
 
 constexpr int kRyserThreads = 256;
 
 int sm_count();
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);   // library memory pool, stream-ordered
+cudaError_t ws_free(void* p, cudaStream_t s);
 
 // host helpers (field.cpp)
 bool is_prime_u32(uint32_t p);

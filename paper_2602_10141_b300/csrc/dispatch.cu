@@ -154,4 +154,297 @@ cudaError_t dispatch_c128(int n, const FpLaunch& L, cudaStream_t s) {
     }
 }
 
+cudaError_t dispatch_x64r(int n, const FpLaunch& L, cudaStream_t s) {
+    const uint64_t items = L.item_end - L.item_begin;
+    if (items == 0) return cudaSuccess;
+    auto grid_for = [&](int bps) {
+        uint64_t want = (items + kRyserThreads - 1) / kRyserThreads;
+        uint64_t cap = (uint64_t)sm_count() * (uint64_t)bps;
+        return (int)(want < cap ? want : cap);
+    };
+    switch (n) {
+        case 1: return launch_x64r<1>(L, grid_for(blocks_per_sm_x64r<1>()), s);
+        case 2: return launch_x64r<2>(L, grid_for(blocks_per_sm_x64r<2>()), s);
+        case 3: return launch_x64r<3>(L, grid_for(blocks_per_sm_x64r<3>()), s);
+        case 4: return launch_x64r<4>(L, grid_for(blocks_per_sm_x64r<4>()), s);
+        case 5: return launch_x64r<5>(L, grid_for(blocks_per_sm_x64r<5>()), s);
+        case 6: return launch_x64r<6>(L, grid_for(blocks_per_sm_x64r<6>()), s);
+        case 7: return launch_x64r<7>(L, grid_for(blocks_per_sm_x64r<7>()), s);
+        case 8: return launch_x64r<8>(L, grid_for(blocks_per_sm_x64r<8>()), s);
+        case 9: return launch_x64r<9>(L, grid_for(blocks_per_sm_x64r<9>()), s);
+        case 10: return launch_x64r<10>(L, grid_for(blocks_per_sm_x64r<10>()), s);
+        case 11: return launch_x64r<11>(L, grid_for(blocks_per_sm_x64r<11>()), s);
+        case 12: return launch_x64r<12>(L, grid_for(blocks_per_sm_x64r<12>()), s);
+        case 13: return launch_x64r<13>(L, grid_for(blocks_per_sm_x64r<13>()), s);
+        case 14: return launch_x64r<14>(L, grid_for(blocks_per_sm_x64r<14>()), s);
+        case 15: return launch_x64r<15>(L, grid_for(blocks_per_sm_x64r<15>()), s);
+        case 16: return launch_x64r<16>(L, grid_for(blocks_per_sm_x64r<16>()), s);
+        case 17: return launch_x64r<17>(L, grid_for(blocks_per_sm_x64r<17>()), s);
+        case 18: return launch_x64r<18>(L, grid_for(blocks_per_sm_x64r<18>()), s);
+        case 19: return launch_x64r<19>(L, grid_for(blocks_per_sm_x64r<19>()), s);
+        case 20: return launch_x64r<20>(L, grid_for(blocks_per_sm_x64r<20>()), s);
+        case 21: return launch_x64r<21>(L, grid_for(blocks_per_sm_x64r<21>()), s);
+        case 22: return launch_x64r<22>(L, grid_for(blocks_per_sm_x64r<22>()), s);
+        case 23: return launch_x64r<23>(L, grid_for(blocks_per_sm_x64r<23>()), s);
+        case 24: return launch_x64r<24>(L, grid_for(blocks_per_sm_x64r<24>()), s);
+        case 25: return launch_x64r<25>(L, grid_for(blocks_per_sm_x64r<25>()), s);
+        case 26: return launch_x64r<26>(L, grid_for(blocks_per_sm_x64r<26>()), s);
+        case 27: return launch_x64r<27>(L, grid_for(blocks_per_sm_x64r<27>()), s);
+        case 28: return launch_x64r<28>(L, grid_for(blocks_per_sm_x64r<28>()), s);
+        case 29: return launch_x64r<29>(L, grid_for(blocks_per_sm_x64r<29>()), s);
+        case 30: return launch_x64r<30>(L, grid_for(blocks_per_sm_x64r<30>()), s);
+        case 31: return launch_x64r<31>(L, grid_for(blocks_per_sm_x64r<31>()), s);
+        case 32: return launch_x64r<32>(L, grid_for(blocks_per_sm_x64r<32>()), s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dispatch_x64c(int n, const FpLaunch& L, cudaStream_t s) {
+    const uint64_t items = L.item_end - L.item_begin;
+    if (items == 0) return cudaSuccess;
+    auto grid_for = [&](int bps) {
+        uint64_t want = (items + kRyserThreads - 1) / kRyserThreads;
+        uint64_t cap = (uint64_t)sm_count() * (uint64_t)bps;
+        return (int)(want < cap ? want : cap);
+    };
+    switch (n) {
+        case 1: return launch_x64c<1>(L, grid_for(blocks_per_sm_x64c<1>()), s);
+        case 2: return launch_x64c<2>(L, grid_for(blocks_per_sm_x64c<2>()), s);
+        case 3: return launch_x64c<3>(L, grid_for(blocks_per_sm_x64c<3>()), s);
+        case 4: return launch_x64c<4>(L, grid_for(blocks_per_sm_x64c<4>()), s);
+        case 5: return launch_x64c<5>(L, grid_for(blocks_per_sm_x64c<5>()), s);
+        case 6: return launch_x64c<6>(L, grid_for(blocks_per_sm_x64c<6>()), s);
+        case 7: return launch_x64c<7>(L, grid_for(blocks_per_sm_x64c<7>()), s);
+        case 8: return launch_x64c<8>(L, grid_for(blocks_per_sm_x64c<8>()), s);
+        case 9: return launch_x64c<9>(L, grid_for(blocks_per_sm_x64c<9>()), s);
+        case 10: return launch_x64c<10>(L, grid_for(blocks_per_sm_x64c<10>()), s);
+        case 11: return launch_x64c<11>(L, grid_for(blocks_per_sm_x64c<11>()), s);
+        case 12: return launch_x64c<12>(L, grid_for(blocks_per_sm_x64c<12>()), s);
+        case 13: return launch_x64c<13>(L, grid_for(blocks_per_sm_x64c<13>()), s);
+        case 14: return launch_x64c<14>(L, grid_for(blocks_per_sm_x64c<14>()), s);
+        case 15: return launch_x64c<15>(L, grid_for(blocks_per_sm_x64c<15>()), s);
+        case 16: return launch_x64c<16>(L, grid_for(blocks_per_sm_x64c<16>()), s);
+        case 17: return launch_x64c<17>(L, grid_for(blocks_per_sm_x64c<17>()), s);
+        case 18: return launch_x64c<18>(L, grid_for(blocks_per_sm_x64c<18>()), s);
+        case 19: return launch_x64c<19>(L, grid_for(blocks_per_sm_x64c<19>()), s);
+        case 20: return launch_x64c<20>(L, grid_for(blocks_per_sm_x64c<20>()), s);
+        case 21: return launch_x64c<21>(L, grid_for(blocks_per_sm_x64c<21>()), s);
+        case 22: return launch_x64c<22>(L, grid_for(blocks_per_sm_x64c<22>()), s);
+        case 23: return launch_x64c<23>(L, grid_for(blocks_per_sm_x64c<23>()), s);
+        case 24: return launch_x64c<24>(L, grid_for(blocks_per_sm_x64c<24>()), s);
+        case 25: return launch_x64c<25>(L, grid_for(blocks_per_sm_x64c<25>()), s);
+        case 26: return launch_x64c<26>(L, grid_for(blocks_per_sm_x64c<26>()), s);
+        case 27: return launch_x64c<27>(L, grid_for(blocks_per_sm_x64c<27>()), s);
+        case 28: return launch_x64c<28>(L, grid_for(blocks_per_sm_x64c<28>()), s);
+        case 29: return launch_x64c<29>(L, grid_for(blocks_per_sm_x64c<29>()), s);
+        case 30: return launch_x64c<30>(L, grid_for(blocks_per_sm_x64c<30>()), s);
+        case 31: return launch_x64c<31>(L, grid_for(blocks_per_sm_x64c<31>()), s);
+        case 32: return launch_x64c<32>(L, grid_for(blocks_per_sm_x64c<32>()), s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int dispatch_blocks_per_sm(int kind, int n) {
+    // kind: 0 modp, 1 f64, 2 c128, 3 x64 real, 4 x64 complex
+    switch (kind) {
+        case 0:
+            switch (n) {
+                case 1: return blocks_per_sm_modp<1>();
+                case 2: return blocks_per_sm_modp<2>();
+                case 3: return blocks_per_sm_modp<3>();
+                case 4: return blocks_per_sm_modp<4>();
+                case 5: return blocks_per_sm_modp<5>();
+                case 6: return blocks_per_sm_modp<6>();
+                case 7: return blocks_per_sm_modp<7>();
+                case 8: return blocks_per_sm_modp<8>();
+                case 9: return blocks_per_sm_modp<9>();
+                case 10: return blocks_per_sm_modp<10>();
+                case 11: return blocks_per_sm_modp<11>();
+                case 12: return blocks_per_sm_modp<12>();
+                case 13: return blocks_per_sm_modp<13>();
+                case 14: return blocks_per_sm_modp<14>();
+                case 15: return blocks_per_sm_modp<15>();
+                case 16: return blocks_per_sm_modp<16>();
+                case 17: return blocks_per_sm_modp<17>();
+                case 18: return blocks_per_sm_modp<18>();
+                case 19: return blocks_per_sm_modp<19>();
+                case 20: return blocks_per_sm_modp<20>();
+                case 21: return blocks_per_sm_modp<21>();
+                case 22: return blocks_per_sm_modp<22>();
+                case 23: return blocks_per_sm_modp<23>();
+                case 24: return blocks_per_sm_modp<24>();
+                case 25: return blocks_per_sm_modp<25>();
+                case 26: return blocks_per_sm_modp<26>();
+                case 27: return blocks_per_sm_modp<27>();
+                case 28: return blocks_per_sm_modp<28>();
+                case 29: return blocks_per_sm_modp<29>();
+                case 30: return blocks_per_sm_modp<30>();
+                case 31: return blocks_per_sm_modp<31>();
+                case 32: return blocks_per_sm_modp<32>();
+                case 33: return blocks_per_sm_modp<33>();
+                case 34: return blocks_per_sm_modp<34>();
+                case 35: return blocks_per_sm_modp<35>();
+                case 36: return blocks_per_sm_modp<36>();
+                case 37: return blocks_per_sm_modp<37>();
+                case 38: return blocks_per_sm_modp<38>();
+                case 39: return blocks_per_sm_modp<39>();
+                case 40: return blocks_per_sm_modp<40>();
+                case 41: return blocks_per_sm_modp<41>();
+                case 42: return blocks_per_sm_modp<42>();
+                case 43: return blocks_per_sm_modp<43>();
+                case 44: return blocks_per_sm_modp<44>();
+                case 45: return blocks_per_sm_modp<45>();
+                case 46: return blocks_per_sm_modp<46>();
+                case 47: return blocks_per_sm_modp<47>();
+                case 48: return blocks_per_sm_modp<48>();
+                default: return 1;
+            }
+        case 1:
+            switch (n) {
+                case 1: return blocks_per_sm_f64<1>();
+                case 2: return blocks_per_sm_f64<2>();
+                case 3: return blocks_per_sm_f64<3>();
+                case 4: return blocks_per_sm_f64<4>();
+                case 5: return blocks_per_sm_f64<5>();
+                case 6: return blocks_per_sm_f64<6>();
+                case 7: return blocks_per_sm_f64<7>();
+                case 8: return blocks_per_sm_f64<8>();
+                case 9: return blocks_per_sm_f64<9>();
+                case 10: return blocks_per_sm_f64<10>();
+                case 11: return blocks_per_sm_f64<11>();
+                case 12: return blocks_per_sm_f64<12>();
+                case 13: return blocks_per_sm_f64<13>();
+                case 14: return blocks_per_sm_f64<14>();
+                case 15: return blocks_per_sm_f64<15>();
+                case 16: return blocks_per_sm_f64<16>();
+                case 17: return blocks_per_sm_f64<17>();
+                case 18: return blocks_per_sm_f64<18>();
+                case 19: return blocks_per_sm_f64<19>();
+                case 20: return blocks_per_sm_f64<20>();
+                case 21: return blocks_per_sm_f64<21>();
+                case 22: return blocks_per_sm_f64<22>();
+                case 23: return blocks_per_sm_f64<23>();
+                case 24: return blocks_per_sm_f64<24>();
+                case 25: return blocks_per_sm_f64<25>();
+                case 26: return blocks_per_sm_f64<26>();
+                case 27: return blocks_per_sm_f64<27>();
+                case 28: return blocks_per_sm_f64<28>();
+                case 29: return blocks_per_sm_f64<29>();
+                case 30: return blocks_per_sm_f64<30>();
+                case 31: return blocks_per_sm_f64<31>();
+                case 32: return blocks_per_sm_f64<32>();
+                default: return 1;
+            }
+        case 2:
+            switch (n) {
+                case 1: return blocks_per_sm_c128<1>();
+                case 2: return blocks_per_sm_c128<2>();
+                case 3: return blocks_per_sm_c128<3>();
+                case 4: return blocks_per_sm_c128<4>();
+                case 5: return blocks_per_sm_c128<5>();
+                case 6: return blocks_per_sm_c128<6>();
+                case 7: return blocks_per_sm_c128<7>();
+                case 8: return blocks_per_sm_c128<8>();
+                case 9: return blocks_per_sm_c128<9>();
+                case 10: return blocks_per_sm_c128<10>();
+                case 11: return blocks_per_sm_c128<11>();
+                case 12: return blocks_per_sm_c128<12>();
+                case 13: return blocks_per_sm_c128<13>();
+                case 14: return blocks_per_sm_c128<14>();
+                case 15: return blocks_per_sm_c128<15>();
+                case 16: return blocks_per_sm_c128<16>();
+                case 17: return blocks_per_sm_c128<17>();
+                case 18: return blocks_per_sm_c128<18>();
+                case 19: return blocks_per_sm_c128<19>();
+                case 20: return blocks_per_sm_c128<20>();
+                case 21: return blocks_per_sm_c128<21>();
+                case 22: return blocks_per_sm_c128<22>();
+                case 23: return blocks_per_sm_c128<23>();
+                case 24: return blocks_per_sm_c128<24>();
+                case 25: return blocks_per_sm_c128<25>();
+                case 26: return blocks_per_sm_c128<26>();
+                case 27: return blocks_per_sm_c128<27>();
+                case 28: return blocks_per_sm_c128<28>();
+                case 29: return blocks_per_sm_c128<29>();
+                case 30: return blocks_per_sm_c128<30>();
+                case 31: return blocks_per_sm_c128<31>();
+                case 32: return blocks_per_sm_c128<32>();
+                default: return 1;
+            }
+        case 3:
+            switch (n) {
+                case 1: return blocks_per_sm_x64r<1>();
+                case 2: return blocks_per_sm_x64r<2>();
+                case 3: return blocks_per_sm_x64r<3>();
+                case 4: return blocks_per_sm_x64r<4>();
+                case 5: return blocks_per_sm_x64r<5>();
+                case 6: return blocks_per_sm_x64r<6>();
+                case 7: return blocks_per_sm_x64r<7>();
+                case 8: return blocks_per_sm_x64r<8>();
+                case 9: return blocks_per_sm_x64r<9>();
+                case 10: return blocks_per_sm_x64r<10>();
+                case 11: return blocks_per_sm_x64r<11>();
+                case 12: return blocks_per_sm_x64r<12>();
+                case 13: return blocks_per_sm_x64r<13>();
+                case 14: return blocks_per_sm_x64r<14>();
+                case 15: return blocks_per_sm_x64r<15>();
+                case 16: return blocks_per_sm_x64r<16>();
+                case 17: return blocks_per_sm_x64r<17>();
+                case 18: return blocks_per_sm_x64r<18>();
+                case 19: return blocks_per_sm_x64r<19>();
+                case 20: return blocks_per_sm_x64r<20>();
+                case 21: return blocks_per_sm_x64r<21>();
+                case 22: return blocks_per_sm_x64r<22>();
+                case 23: return blocks_per_sm_x64r<23>();
+                case 24: return blocks_per_sm_x64r<24>();
+                case 25: return blocks_per_sm_x64r<25>();
+                case 26: return blocks_per_sm_x64r<26>();
+                case 27: return blocks_per_sm_x64r<27>();
+                case 28: return blocks_per_sm_x64r<28>();
+                case 29: return blocks_per_sm_x64r<29>();
+                case 30: return blocks_per_sm_x64r<30>();
+                case 31: return blocks_per_sm_x64r<31>();
+                case 32: return blocks_per_sm_x64r<32>();
+                default: return 1;
+            }
+        case 4:
+            switch (n) {
+                case 1: return blocks_per_sm_x64c<1>();
+                case 2: return blocks_per_sm_x64c<2>();
+                case 3: return blocks_per_sm_x64c<3>();
+                case 4: return blocks_per_sm_x64c<4>();
+                case 5: return blocks_per_sm_x64c<5>();
+                case 6: return blocks_per_sm_x64c<6>();
+                case 7: return blocks_per_sm_x64c<7>();
+                case 8: return blocks_per_sm_x64c<8>();
+                case 9: return blocks_per_sm_x64c<9>();
+                case 10: return blocks_per_sm_x64c<10>();
+                case 11: return blocks_per_sm_x64c<11>();
+                case 12: return blocks_per_sm_x64c<12>();
+                case 13: return blocks_per_sm_x64c<13>();
+                case 14: return blocks_per_sm_x64c<14>();
+                case 15: return blocks_per_sm_x64c<15>();
+                case 16: return blocks_per_sm_x64c<16>();
+                case 17: return blocks_per_sm_x64c<17>();
+                case 18: return blocks_per_sm_x64c<18>();
+                case 19: return blocks_per_sm_x64c<19>();
+                case 20: return blocks_per_sm_x64c<20>();
+                case 21: return blocks_per_sm_x64c<21>();
+                case 22: return blocks_per_sm_x64c<22>();
+                case 23: return blocks_per_sm_x64c<23>();
+                case 24: return blocks_per_sm_x64c<24>();
+                case 25: return blocks_per_sm_x64c<25>();
+                case 26: return blocks_per_sm_x64c<26>();
+                case 27: return blocks_per_sm_x64c<27>();
+                case 28: return blocks_per_sm_x64c<28>();
+                case 29: return blocks_per_sm_x64c<29>();
+                case 30: return blocks_per_sm_x64c<30>();
+                case 31: return blocks_per_sm_x64c<31>();
+                case 32: return blocks_per_sm_x64c<32>();
+                default: return 1;
+            }
+        default: return 1;
+    }
+}
+
 }  // namespace permx

@@ -9,10 +9,13 @@
 //   4 mad.lo.u32   5 mul.wide.u32 6 mul.hi.u32   7 add.u32   8 min.u32
 //   9 one F_p unit (modular add + Montgomery multiply, as in the F_p walk)
 //  10 one float64 unit (add + multiply)  11 one complex128 unit (2 adds + complex multiply)
+//  12 clz.b64   13 clz.b32   14 one real integer-mantissa factor (x64_mul)
+//  15 one complex integer-mantissa factor (x64c_mul)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "common.cuh"
+#include "x64_arith.cuh"
 
 namespace permx {
 
@@ -62,6 +65,22 @@ __global__ void peak_kernel(int iters, uint32_t seed, unsigned long long* sink) 
             if (KIND == 10) {
                 d[k] = d[k] + f;
                 d[k] = d[k] * e;
+            }
+            if (KIND == 12) {
+                uint32_t z;
+                asm volatile("clz.b64 %0, %1;" : "=r"(z) : "l"((unsigned long long)u[k] << 20 | t[k]));
+                u[k] += z;
+            }
+            if (KIND == 13) asm volatile("clz.b32 %0, %0;" : "+r"(u[k]));
+            if (KIND == 14) {
+                XReal x{(int64_t)(((uint64_t)u[k] << 29) | 0x2000000000000000ull), 0};
+                x = x64_mul(x, (int64_t)((uint64_t)v << 28) + t[k], 0);
+                u[k] = (uint32_t)x.m ^ (uint32_t)x.e;
+            }
+            if (KIND == 15) {
+                XCplx x{(int64_t)(((uint64_t)u[k] << 28) | 0x1000000000000000ull), (int64_t)t[k] << 30, 0};
+                x = x64c_mul(x, (int64_t)((uint64_t)v << 28) + t[k], (int64_t)w << 27, 0);
+                u[k] = (uint32_t)x.re ^ (uint32_t)x.im ^ (uint32_t)x.e;
             }
             if (KIND == 11) {
                 cr[k].x += f;
@@ -118,6 +137,10 @@ extern "C" int permx_peak_probe(int kind, int blocks, int threads, int iters, do
         case 9: e = run_probe<9>(blocks, threads, iters, sink, &ms); break;
         case 10: e = run_probe<10>(blocks, threads, iters, sink, &ms); break;
         case 11: e = run_probe<11>(blocks, threads, iters, sink, &ms); break;
+        case 12: e = run_probe<12>(blocks, threads, iters, sink, &ms); break;
+        case 13: e = run_probe<13>(blocks, threads, iters, sink, &ms); break;
+        case 14: e = run_probe<14>(blocks, threads, iters, sink, &ms); break;
+        case 15: e = run_probe<15>(blocks, threads, iters, sink, &ms); break;
         default: break;
     }
     cudaFree(sink);

@@ -1,0 +1,232 @@
+// Gray-code Ryser for float64 / complex128 matrices on the integer pipes
+// ("x64" arithmetic; paper §2.2 walk, Nijenhuis-Wilf form).
+//
+// B300 executes FP64 at about 1/74 of its FP32 rate, while 32-bit integer
+// multiplies and adds issue at 1/2 to 1/1 of it.  This walk therefore keeps
+// everything in integers:
+//  - row i is scaled by 2^sigma_i (sum_j |a_ij| 2^sigma_i < 2^61) and rounded
+//    to even int64 entries A_ij, so every Gray-walk row sum
+//    R_i = X_i + sum_{j in S} A_ij is exact (no drift, no rounding);
+//  - a product of row sums is a float with a signed 62-bit mantissa m
+//    (|m| in [2^61, 2^62], complex: the larger component in [2^60, 2^61]) and
+//    an int exponent; each factor is one truncated 64x64 -> 128-bit product
+//    from three signed 32x32 -> 64-bit multiplies, then a leading-zero
+//    normalisation;
+//  - each chunk sums its terms exactly into a 128-bit fixed-point
+//    accumulator whose exponent follows the chunk's first term, and hands the
+//    chunk total on as a double-double scaled back by 2^-sum(sigma).
+// Relative precision per factor is about 2^-59 (float64: 2^-53).
+#pragma once
+#include "common.cuh"
+#include "ryser_fp.cuh"
+#include "x64_arith.cuh"
+
+namespace permx {
+
+// ---------------------------------------------------------------------------
+// kernels.  Staged layout per matrix (int64 words): columns 0..n-1 of A,
+// column n = X (Nijenhuis-Wilf offset), each `ld` entries (complex: re, im
+// interleaved per entry), then one word holding -sum_i sigma_i.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64r_kernel(const FpLaunch L) {
+    constexpr int NP = pad2(N);
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    const int lg = L.log2_chunks >= 5 ? 5 : L.log2_chunks;
+    const int G = 1 << lg;
+    for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         base < L.item_end; base += stride) {
+        const uint64_t item = base + lane;
+        double s = 0.0, comp = 0.0;
+        bool valid = item < L.item_end;
+        const double* cold = L.colT;
+        uint64_t c = 0, slot = 0;
+        if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
+        if (valid) {
+            const int64_t* col = reinterpret_cast<const int64_t*>(cold);
+            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            int64_t R[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) R[i] = col[N * NP + i];             // X_i
+            const uint64_t S0 = ks ^ (ks >> 1);
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                if (!((S0 >> j) & 1)) continue;
+                const longlong2* c2 = reinterpret_cast<const longlong2*>(col + j * NP);
+#pragma unroll
+                for (int q = 0; q < NP / 2; ++q) {
+                    const longlong2 v = __ldg(c2 + q);
+                    R[2 * q] += v.x;
+                    if (2 * q + 1 < N) R[2 * q + 1] += v.y;
+                }
+            }
+            const int scale = (int)col[(N + 1) * NP];
+            XAcc acc;
+            x64_acc_init(acc);
+            for (uint64_t k = ks; k < ke; ++k) {
+                if (k > ks) {
+                    const int j = __ffsll((long long)k) - 1;
+                    const longlong2* c2 = reinterpret_cast<const longlong2*>(col + j * NP);
+                    if ((k >> (j + 1)) & 1) {
+#pragma unroll
+                        for (int q = 0; q < NP / 2; ++q) {
+                            const longlong2 v = __ldg(c2 + q);
+                            R[2 * q] -= v.x;
+                            if (2 * q + 1 < N) R[2 * q + 1] -= v.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NP / 2; ++q) {
+                            const longlong2 v = __ldg(c2 + q);
+                            R[2 * q] += v.x;
+                            if (2 * q + 1 < N) R[2 * q + 1] += v.y;
+                        }
+                    }
+                }
+                // four interleaved product chains, then combined
+                XReal t[4];
+#pragma unroll
+                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64_from_int(R[q]);
+#pragma unroll
+                for (int i = 4; i < N; ++i) t[i & 3] = x64_mul(t[i & 3], R[i], 0);
+                XReal p = t[0];
+                if (N >= 2) p = x64_mul(p, t[1].m, t[1].e);
+                if (N >= 4) {
+                    const XReal p23 = x64_mul(t[2], t[3].m, t[3].e);
+                    p = x64_mul(p, p23.m, p23.e);
+                } else if (N == 3) {
+                    p = x64_mul(p, t[2].m, t[2].e);
+                }
+                x64_acc_add(acc, p.m, p.e, k & 1);
+            }
+            x64_acc_to_dd(acc, scale, s, comp);
+        }
+        group_reduce(s, comp, G);
+        if ((lane & (G - 1)) == 0 && valid) reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64c_kernel(const FpLaunch L) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    const int lg = L.log2_chunks >= 5 ? 5 : L.log2_chunks;
+    const int G = 1 << lg;
+    for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         base < L.item_end; base += stride) {
+        const uint64_t item = base + lane;
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        bool valid = item < L.item_end;
+        const double* cold = L.colT;
+        uint64_t c = 0, slot = 0;
+        if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
+        if (valid) {
+            const longlong2* col = reinterpret_cast<const longlong2*>(cold);
+            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            int64_t Rr[N], Ri[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const longlong2 x = __ldg(col + N * N + i);
+                Rr[i] = x.x;
+                Ri[i] = x.y;
+            }
+            const uint64_t S0 = ks ^ (ks >> 1);
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                if (!((S0 >> j) & 1)) continue;
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const longlong2 v = __ldg(col + j * N + i);
+                    Rr[i] += v.x;
+                    Ri[i] += v.y;
+                }
+            }
+            const int scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
+            XAcc ar, ai;
+            x64_acc_init(ar);
+            x64_acc_init(ai);
+            for (uint64_t k = ks; k < ke; ++k) {
+                if (k > ks) {
+                    const int j = __ffsll((long long)k) - 1;
+                    if ((k >> (j + 1)) & 1) {
+#pragma unroll
+                        for (int i = 0; i < N; ++i) {
+                            const longlong2 v = __ldg(col + j * N + i);
+                            Rr[i] -= v.x;
+                            Ri[i] -= v.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < N; ++i) {
+                            const longlong2 v = __ldg(col + j * N + i);
+                            Rr[i] += v.x;
+                            Ri[i] += v.y;
+                        }
+                    }
+                }
+                XCplx t[4];
+#pragma unroll
+                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+#pragma unroll
+                for (int i = 4; i < N; ++i) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+                XCplx p = t[0];
+                if (N >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
+                if (N >= 4) {
+                    const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
+                    p = x64c_mul(p, p23.re, p23.im, p23.e);
+                } else if (N == 3) {
+                    p = x64c_mul(p, t[2].re, t[2].im, t[2].e);
+                }
+                x64_acc_add(ar, p.re, p.e, k & 1);
+                x64_acc_add(ai, p.im, p.e, k & 1);
+            }
+            x64_acc_to_dd(ar, scale, sr, cr);
+            x64_acc_to_dd(ai, scale, si, ci);
+        }
+        group_reduce(sr, cr, G);
+        group_reduce(si, ci, G);
+        if ((lane & (G - 1)) == 0 && valid) {
+            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
+            out[0] = make_double2(sr, cr);
+            out[1] = make_double2(si, ci);
+        }
+    }
+}
+
+template <int N>
+cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s) {
+    ryser_x64r_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+template <int N>
+cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s) {
+    ryser_x64c_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+template <int N>
+int blocks_per_sm_x64r() {
+    static int cached = -1;
+    if (cached < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64r_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+template <int N>
+int blocks_per_sm_x64c() {
+    static int cached = -1;
+    if (cached < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        cached = b;
+    }
+    return cached;
+}
+
+}  // namespace permx

@@ -33,9 +33,9 @@ int ModpRange::init(const uint32_t* A_dev, int n_, uint32_t p_, int nw_, cudaStr
     ell = chunk_log2_modp(bits);
     ld = pad4(n);
     const size_t words = (size_t)(n + nw) * ld;
-    PERMX_CUDA(cudaMallocAsync(&col, sizeof(uint32_t) * words + 256, s));
+    PERMX_CUDA(ws_alloc(reinterpret_cast<void**>(&col), sizeof(uint32_t) * words + 256, s));
     acc = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(col) + ((sizeof(uint32_t) * words + 15) & ~size_t(15)));
-    PERMX_CUDA(cudaMallocAsync(&params, 256, s));
+    PERMX_CUDA(ws_alloc(reinterpret_cast<void**>(&params), 256, s));
     const uint32_t hp[2] = {p, inv_mod_2_32(p)};
     PERMX_CUDA(cudaMemcpyAsync(params, hp, sizeof hp, cudaMemcpyHostToDevice, s));
     PERMX_CUDA(stage_columns_u32(A_dev, n, ld, p, nw, col, s));
@@ -72,8 +72,8 @@ int ModpRange::run(uint64_t k0, uint64_t k1, uint32_t* residue) {
 }
 
 void ModpRange::release() {
-    if (col) cudaFreeAsync(col, s);
-    if (params) cudaFreeAsync(params, s);
+    if (col) ws_free(col, s);
+    if (params) ws_free(params, s);
     col = nullptr;
     params = nullptr;
     acc = nullptr;
@@ -201,7 +201,7 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
     cudaStream_t s;
     PERMX_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     uint32_t* dA = nullptr;
-    cudaError_t e = cudaMallocAsync(&dA, sizeof(uint32_t) * n * n, s);
+    cudaError_t e = ws_alloc(reinterpret_cast<void**>(&dA), sizeof(uint32_t) * n * n, s);
     if (e != cudaSuccess) {
         cudaStreamDestroy(s);
         return cuda_fail(e, "cudaMallocAsync");
@@ -243,7 +243,7 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
         R.release();
         if (rc) break;
     }
-    cudaFreeAsync(dA, s);
+    ws_free(dA, s);
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc == PERMX_EAGAIN) return fail(PERMX_EAGAIN, "stopped after the requested number of slices");

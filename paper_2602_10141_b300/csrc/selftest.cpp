@@ -1,0 +1,60 @@
+// CPU entry points for the integer-mantissa helpers (include/permx_selftest.h).
+// They call the very functions the float64 / complex128 kernels inline.
+#include "permx_selftest.h"
+#include "x64_arith.cuh"
+
+using namespace permx;
+
+extern "C" {
+
+int64_t permx_x64_mulhi62(int64_t a, int64_t b) { return x64_mulhi62(a, b); }
+
+int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {
+    if (!R || !m_out || !e_out || n < 1 || n > 64) return -1;
+    XReal t[4];
+    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64_from_int(R[q]);
+    for (int i = 4; i < n; ++i) t[i & 3] = x64_mul(t[i & 3], R[i], 0);
+    XReal p = t[0];
+    if (n >= 2) p = x64_mul(p, t[1].m, t[1].e);
+    if (n >= 4) {
+        const XReal p23 = x64_mul(t[2], t[3].m, t[3].e);
+        p = x64_mul(p, p23.m, p23.e);
+    } else if (n == 3) {
+        p = x64_mul(p, t[2].m, t[2].e);
+    }
+    *m_out = p.m;
+    *e_out = p.e;
+    return 0;
+}
+
+int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t* re_out, int64_t* im_out,
+                       int32_t* e_out) {
+    if (!Rr || !Ri || !re_out || !im_out || !e_out || n < 1 || n > 64) return -1;
+    XCplx t[4];
+    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+    for (int i = 4; i < n; ++i) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+    XCplx p = t[0];
+    if (n >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
+    if (n >= 4) {
+        const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
+        p = x64c_mul(p, p23.re, p23.im, p23.e);
+    } else if (n == 3) {
+        p = x64c_mul(p, t[2].re, t[2].im, t[2].e);
+    }
+    *re_out = p.re;
+    *im_out = p.im;
+    *e_out = p.e;
+    return 0;
+}
+
+int permx_x64_accumulate(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count, int32_t scale,
+                         double* hi, double* lo) {
+    if (!m || !e || !neg || !hi || !lo || count < 0 || count > 4096) return -1;
+    XAcc a;
+    x64_acc_init(a);
+    for (int k = 0; k < count; ++k) x64_acc_add(a, m[k], e[k], neg[k] != 0);
+    x64_acc_to_dd(a, scale, *hi, *lo);
+    return 0;
+}
+
+}  // extern "C"

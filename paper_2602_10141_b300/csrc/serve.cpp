@@ -95,6 +95,7 @@ struct Request {
     uint32_t p = 0;
     std::vector<unsigned char> host;   // row-major matrix
     int ell = 0, log2_chunks = 0, lg = 0, ld = 0;
+    bool x64 = false;                  // float fields: integer-mantissa walk
     uint64_t chunks = 0, next_chunk = 0;
     int64_t arena_off = -1;            // columns, then partial slots / accumulator
     size_t bytes = 0, col_bytes = 0;
@@ -105,18 +106,19 @@ struct Request {
 
 int entry_bytes(int field) { return field == PERMX_FIELD_C128 ? 16 : field == PERMX_FIELD_F64 ? 8 : 4; }
 
-// estimated device time per (subset, row) term in picoseconds on one B300
-// (complex128 ~6 and float64 ~2 FP64 instructions per term, F_p ~9 integer ones)
-double term_cost_ps(int field) { return field == PERMX_FIELD_C128 ? 12.0 : field == PERMX_FIELD_F64 ? 5.0 : 0.4; }
 
 }  // namespace
 }  // namespace permx
 
 using namespace permx;
 
+constexpr int kSideStreams = 4;
+
 struct perm_server {
     perm_serve_cfg cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t side[kSideStreams] = {nullptr};
+    cudaEvent_t ev_ready = nullptr, ev_side[kSideStreams] = {nullptr};
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -128,6 +130,7 @@ struct perm_server {
     int64_t submitted = 0, completed = 0;
     std::atomic<int64_t> steps{0}, launches{0};
     int worker_error = 0;
+    bool x64 = true;                   // float arithmetic fixed when the server is created
     std::string worker_msg;
     // device / pinned buffers owned by the worker
     unsigned char* arena_base = nullptr;
@@ -172,16 +175,18 @@ int grow_pinned(unsigned char** p, size_t* cap, size_t need) {
     return PERMX_OK;
 }
 
-void plan_request(Request* r) {
+void plan_request(Request* r, bool x64) {
     const bool modp = r->field == PERMX_FIELD_MODP;
     // the batched path's plan: Nijenhuis-Wilf form, same chunking
     const int bits = walk_bits(r->n, 1);
-    r->ell = modp ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+    r->ell = chunk_log2((Field)r->field, r->n, bits);
     r->log2_chunks = bits - r->ell;
     r->lg = r->log2_chunks >= 5 ? 5 : r->log2_chunks;
     r->chunks = 1ull << r->log2_chunks;
     r->ld = modp ? pad4(r->n) : r->field == PERMX_FIELD_F64 ? pad2(r->n) : r->n;
-    r->col_bytes = align256((size_t)(r->n + 1) * r->ld * entry_bytes(r->field));
+    r->x64 = !modp && x64;
+    // staged columns (plus the x column); the integer-mantissa layout adds a scale word pair
+    r->col_bytes = align256((size_t)(r->n + 1) * r->ld * entry_bytes(r->field) + (r->x64 ? 16 : 0));
     const size_t tail = modp ? 8 : (size_t)(r->chunks >> r->lg) * (r->field == PERMX_FIELD_C128 ? 32 : 16);
     r->bytes = r->col_bytes + align256(tail);
 }
@@ -196,18 +201,20 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
         int rc = grow_pinned(&S->h_upload, &S->h_upload_cap, up);
         if (!rc) rc = grow_device(&S->d_upload, &S->d_upload_cap, up);
         if (rc) return rc;
-        std::vector<StageDesc> sd[3];
+        std::vector<StageDesc> sd[3], sx[2];   // sx: integer-mantissa staging [complex, real]
         size_t o = 0;
         for (Request* r : admitted) {
             std::memcpy(S->h_upload + o, r->host.data(), r->host.size());
             const int eb = entry_bytes(r->field);
-            sd[r->field].push_back(
-                StageDesc{(int64_t)(o / eb), (int64_t)(r->arena_off / eb), r->n, r->ld, r->p, 1});
+            const StageDesc d{(int64_t)(o / eb), (int64_t)(r->arena_off / eb), r->n, r->ld, r->p, 1};
+            if (r->x64) sx[r->field == PERMX_FIELD_C128 ? 0 : 1].push_back(d);
+            else sd[r->field].push_back(d);
             o += align256(r->host.size());
         }
         PERMX_CUDA(cudaMemcpyAsync(S->d_upload, S->h_upload, up, cudaMemcpyHostToDevice, st));
         size_t meta = 0;
         for (auto& v : sd) meta += align256(v.size() * sizeof(StageDesc));
+        for (auto& v : sx) meta += align256(v.size() * sizeof(StageDesc));
         rc = grow_pinned(&S->h_meta, &S->h_meta_cap, meta);
         if (!rc) rc = grow_device(&S->d_meta, &S->d_meta_cap, meta);
         if (rc) return rc;
@@ -216,6 +223,11 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             if (sd[f].empty()) continue;
             std::memcpy(S->h_meta + mo, sd[f].data(), sd[f].size() * sizeof(StageDesc));
             mo += align256(sd[f].size() * sizeof(StageDesc));
+        }
+        for (int f = 0; f < 2; ++f) {
+            if (sx[f].empty()) continue;
+            std::memcpy(S->h_meta + mo, sx[f].data(), sx[f].size() * sizeof(StageDesc));
+            mo += align256(sx[f].size() * sizeof(StageDesc));
         }
         PERMX_CUDA(cudaMemcpyAsync(S->d_meta, S->h_meta, mo, cudaMemcpyHostToDevice, st));
         mo = 0;
@@ -226,6 +238,13 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             ++S->launches;
             mo += align256(sd[f].size() * sizeof(StageDesc));
         }
+        for (int f = 0; f < 2; ++f) {
+            if (sx[f].empty()) continue;
+            PERMX_CUDA(launch_stage_x64(f == 0, S->d_upload, reinterpret_cast<const StageDesc*>(S->d_meta + mo),
+                                        (int64_t)sx[f].size(), S->arena_base, st));
+            ++S->launches;
+            mo += align256(sx[f].size() * sizeof(StageDesc));
+        }
         // F_p accumulators start at zero
         for (Request* r : admitted)
             if (r->field == PERMX_FIELD_MODP)
@@ -235,45 +254,39 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
     }
 
     // ---- grant work ----------------------------------------------------------------------
+    // A chunk is one thread's Gray walk.  Per step every (field, n) class may
+    // run one wave of its kernel's resident threads (classes run concurrently
+    // on the side streams), or chunks_per_step chunks in total when set.
+    // Within a class every request first gets a fair share (at least one lane
+    // group), then the rest of the wave goes to the oldest requests first.
     std::vector<Request*> act = S->resident;   // admission order
-    double budget_ps = S->cfg.chunks_per_step > 0 ? 0.0 : 2.0e9;   // 2 ms of estimated device time
     std::vector<uint64_t> grant(act.size(), 0);
-    auto group_cost = [](Request* r) {
-        const uint64_t G = 1ull << r->lg;
-        return (double)G * (double)(1ull << r->ell) * r->n * term_cost_ps(r->field);
-    };
-    if (S->cfg.chunks_per_step > 0) {
-        // fixed chunk budget: every request one group, then the rest oldest first
-        int64_t left = S->cfg.chunks_per_step;
-        for (size_t i = 0; i < act.size(); ++i) {
+    std::map<std::pair<int, int>, std::vector<size_t>> by_class;
+    for (size_t i = 0; i < act.size(); ++i) by_class[{act[i]->field, act[i]->n}].push_back(i);
+    const int64_t fixed = S->cfg.chunks_per_step;
+    for (auto& kv : by_class) {
+        const std::vector<size_t>& idx = kv.second;
+        Request* r0 = act[idx[0]];
+        const int kind = r0->field == PERMX_FIELD_MODP ? 0
+                         : r0->field == PERMX_FIELD_F64 ? (r0->x64 ? 3 : 1) : (r0->x64 ? 4 : 2);
+        int64_t budget = fixed > 0 ? std::max<int64_t>(1, fixed / (int64_t)by_class.size())
+                                   : (int64_t)sm_count() * dispatch_blocks_per_sm(kind, r0->n) * kRyserThreads;
+        const int64_t share = budget / (2 * (int64_t)idx.size());
+        for (size_t i : idx) {
             const uint64_t G = 1ull << act[i]->lg;
-            grant[i] = G;
-            left -= (int64_t)G;
+            const uint64_t rem = act[i]->chunks - act[i]->next_chunk;
+            grant[i] = std::min(std::max<uint64_t>(G, (uint64_t)share / G * G), rem);
+            budget -= (int64_t)grant[i];
         }
-        for (size_t i = 0; i < act.size() && left > 0; ++i) {
+        for (size_t i : idx) {
+            if (budget <= 0) break;
             const uint64_t G = 1ull << act[i]->lg;
             const uint64_t rem = act[i]->chunks - act[i]->next_chunk - grant[i];
-            uint64_t extra = std::min<uint64_t>(rem, (uint64_t)left / G * G);
+            const uint64_t extra = std::min<uint64_t>(rem, (uint64_t)budget / G * G);
             grant[i] += extra;
-            left -= (int64_t)extra;
-        }
-    } else {
-        for (size_t i = 0; i < act.size(); ++i) {
-            grant[i] = 1ull << act[i]->lg;
-            budget_ps -= group_cost(act[i]);
-        }
-        for (size_t i = 0; i < act.size() && budget_ps > 0; ++i) {
-            const uint64_t G = 1ull << act[i]->lg;
-            const uint64_t rem = (act[i]->chunks - act[i]->next_chunk - grant[i]) / G;
-            uint64_t groups = (uint64_t)(budget_ps / group_cost(act[i]));
-            groups = std::min(groups, rem);
-            grant[i] += groups * G;
-            budget_ps -= groups * group_cost(act[i]);
+            budget -= (int64_t)extra;
         }
     }
-    for (size_t i = 0; i < act.size(); ++i)
-        grant[i] = std::min<uint64_t>(grant[i], act[i]->chunks - act[i]->next_chunk);
-
     // ---- segment tables, one launch per (field, n) ------------------------------------------
     std::map<std::pair<int, int>, std::vector<size_t>> classes;
     for (size_t i = 0; i < act.size(); ++i)
@@ -313,7 +326,12 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
         mo += align256(kv.second.size() * sizeof(SegDesc));
     }
     if (mo) PERMX_CUDA(cudaMemcpyAsync(S->d_meta, S->h_meta, mo, cudaMemcpyHostToDevice, st));
+    // classes run on side streams so that small and large classes overlap
+    PERMX_CUDA(cudaEventRecord(S->ev_ready, st));
+    for (int q = 0; q < kSideStreams; ++q) PERMX_CUDA(cudaStreamWaitEvent(S->side[q], S->ev_ready, 0));
+    int li = 0;
     for (const L& l : launches) {
+        cudaStream_t ls = S->side[li++ % kSideStreams];
         const SegDesc* segs = reinterpret_cast<const SegDesc*>(S->d_meta + l.off);
         cudaError_t e;
         if (l.field == PERMX_FIELD_MODP) {
@@ -331,7 +349,7 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             M.segs = segs;
             M.nsegs = l.nseg;
             M.nw = 1;
-            e = dispatch_modp(l.n, M, st);
+            e = dispatch_modp(l.n, M, ls);
         } else {
             FpLaunch F;
             F.colT = reinterpret_cast<const double*>(S->arena_base);
@@ -344,10 +362,15 @@ int run_step(perm_server* S, std::vector<Request*>& admitted) {
             F.segs = segs;
             F.nsegs = l.nseg;
             F.nw = 1;
-            e = l.field == PERMX_FIELD_C128 ? dispatch_c128(l.n, F, st) : dispatch_f64(l.n, F, st);
+            if (l.any->x64) e = l.field == PERMX_FIELD_C128 ? dispatch_x64c(l.n, F, ls) : dispatch_x64r(l.n, F, ls);
+            else e = l.field == PERMX_FIELD_C128 ? dispatch_c128(l.n, F, ls) : dispatch_f64(l.n, F, ls);
         }
         if (e != cudaSuccess) return cuda_fail(e, "server step launch");
         ++S->launches;
+    }
+    for (int q = 0; q < kSideStreams; ++q) {
+        PERMX_CUDA(cudaEventRecord(S->ev_side[q], S->side[q]));
+        PERMX_CUDA(cudaStreamWaitEvent(st, S->ev_side[q], 0));
     }
     for (size_t i = 0; i < act.size(); ++i) act[i]->next_chunk += grant[i];
 
@@ -526,6 +549,11 @@ int serve_create(const perm_serve_cfg* cfg, perm_server** h) {
     if (S->cfg.chunks_per_step < 0) S->cfg.chunks_per_step = 0;
     cudaError_t e = cudaSetDevice(S->cfg.device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    for (int q = 0; q < kSideStreams && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&S->side[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_side[q], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_ready, cudaEventDisableTiming);
     if (e == cudaSuccess && !S->cfg.plain_fifo)
         e = cudaMalloc(reinterpret_cast<void**>(&S->arena_base), (size_t)S->cfg.device_bytes);
     if (e != cudaSuccess) {
@@ -534,6 +562,7 @@ int serve_create(const perm_serve_cfg* cfg, perm_server** h) {
         return cuda_fail(e, "serve_create");
     }
     S->arena.reset(S->cfg.plain_fifo ? 0 : (size_t)S->cfg.device_bytes);
+    S->x64 = fp_arith() == 1;
     S->worker = std::thread(worker_main, S);
     *h = S;
     return PERMX_OK;
@@ -558,7 +587,7 @@ int serve_submit(perm_server* S, int field, int32_t n, const void* A_host, uint3
     r->p = p;
     const size_t bytes = (size_t)n * n * entry_bytes(field);
     r->host.assign(static_cast<const unsigned char*>(A_host), static_cast<const unsigned char*>(A_host) + bytes);
-    plan_request(r);
+    plan_request(r, S->x64);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->worker_error) {
@@ -653,6 +682,11 @@ int serve_destroy(perm_server* S) {
     if (S->d_upload) cudaFree(S->d_upload);
     if (S->h_meta) cudaFreeHost(S->h_meta);
     if (S->h_upload) cudaFreeHost(S->h_upload);
+    for (int q = 0; q < kSideStreams; ++q) {
+        if (S->side[q]) cudaStreamDestroy(S->side[q]);
+        if (S->ev_side[q]) cudaEventDestroy(S->ev_side[q]);
+    }
+    if (S->ev_ready) cudaEventDestroy(S->ev_ready);
     cudaStreamDestroy(S->stream);
     delete S;
     return PERMX_OK;

@@ -1,0 +1,138 @@
+// Integer-mantissa arithmetic for the float64 / complex128 Gray walks
+// (host + device; the kernels are in ryser_x64.cuh).  See ryser_x64.cuh for
+// the representation.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#if !defined(__CUDACC__) && !defined(__host__)
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace permx {
+
+// ---------------------------------------------------------------------------
+// arithmetic helpers (host+device so that the library's self-test can check
+// them against exact 128-bit arithmetic on the CPU)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int x64_clz(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// (a * b) >> 62 for |a|, |b| <= 2^62 (so the result fits), truncated: the
+// result is within [-2, +1] of floor(a*b / 2^62).  Balanced 32-bit limbs
+// a = a1 2^32 + a0 with a0 in [-2^31, 2^31) keep every partial product a
+// signed 32x32 -> 64 multiply; a0*b0 (< 2^62 in size) is dropped.
+__host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
+    const int32_t a0 = (int32_t)(uint32_t)(uint64_t)a;
+    const int32_t b0 = (int32_t)(uint32_t)(uint64_t)b;
+    const int32_t a1 = (int32_t)((a - (int64_t)a0) >> 32);
+    const int32_t b1 = (int32_t)((b - (int64_t)b0) >> 32);
+    const int64_t hh = (int64_t)a1 * (int64_t)b1;
+    const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
+    return hh * 4 + (mid >> 30);
+}
+
+// Left shift that puts the top bit of |x| at position T-1, i.e. |x| in
+// [2^(T-1), 2^T] (0 stays 0); mag_or is |x| (or an OR of several |.|).
+template <int T>
+__host__ __device__ __forceinline__ int x64_norm_shift(uint64_t mag_or) {
+    const int lz = x64_clz(mag_or | 1ull);
+    const int s = lz - (64 - T);
+    return s > 0 ? s : 0;
+}
+__host__ __device__ __forceinline__ uint64_t x64_mag(int64_t x) { return (uint64_t)(x ^ (x >> 63)); }
+
+struct XReal { int64_t m; int e; };
+struct XCplx { int64_t re, im; int e; };
+
+// real: mantissa target |m| in [2^61, 2^62]
+__host__ __device__ __forceinline__ XReal x64_from_int(int64_t r) {
+    const int s = x64_norm_shift<62>(x64_mag(r));
+    return XReal{r << s, -s};
+}
+__host__ __device__ __forceinline__ XReal x64_mul(XReal a, int64_t m2, int e2) {
+    const int64_t x = x64_mulhi62(a.m, m2);
+    const int s = x64_norm_shift<62>(x64_mag(x));
+    return XReal{x << s, a.e + e2 + 62 - s};
+}
+
+// complex: larger component target in [2^60, 2^61] (sums of two stay below 2^62)
+__host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) {
+    const int s = x64_norm_shift<61>(x64_mag(re) | x64_mag(im));
+    return XCplx{re << s, im << s, -s};
+}
+// (a.re + i a.im) * (br + i bi), |br|, |bi| <= 2^61; three products (Karatsuba)
+__host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t bi, int eb) {
+    const int64_t k1 = x64_mulhi62(a.re + a.im, br);
+    const int64_t k2 = x64_mulhi62(a.re, bi - br);
+    const int64_t k3 = x64_mulhi62(a.im, br + bi);
+    const int64_t re = k1 - k3, im = k1 + k2;
+    const int s = x64_norm_shift<61>(x64_mag(re) | x64_mag(im));
+    return XCplx{re << s, im << s, a.e + eb + 62 - s};
+}
+
+// Exact fixed-point sum of one chunk's terms: value = acc * 2^E.  The first
+// term fixes E 24 bits below its mantissa's lowest bit range; a term more
+// than 2^40 above the accumulator scale rescales it first, so at most 2^12
+// terms never overflow 128 bits.  Terms far below (shift < -62) round to 0.
+struct XAcc {
+    __int128 acc;
+    int E;
+    bool set;
+};
+__host__ __device__ __forceinline__ void x64_acc_init(XAcc& a) {
+    a.acc = 0;
+    a.E = 0;
+    a.set = false;
+}
+__host__ __device__ __forceinline__ void x64_acc_add(XAcc& a, int64_t m, int e, bool negate) {
+    if (m == 0) return;
+    if (!a.set) {
+        a.E = e - 24;
+        a.set = true;
+    }
+    int sh = e - a.E;
+    if (sh > 40) {                     // rare: a much larger term, rescale the accumulator
+        const int d = sh - 40;
+        a.acc = d < 127 ? (a.acc >> d) : (a.acc < 0 ? -1 : 0);
+        a.E += d;
+        sh = 40;
+    }
+    __int128 v;
+    if (sh >= 0) v = (__int128)m << sh;
+    else if (sh > -63) v = (__int128)(m >> (-sh));
+    else return;
+    a.acc = negate ? a.acc - v : a.acc + v;
+}
+// acc * 2^(E + scale) as a double-double (hi + lo)
+__host__ __device__ __forceinline__ void x64_acc_to_dd(const XAcc& a, int scale, double& hi, double& lo) {
+    if (!a.set || a.acc == 0) {
+        hi = 0.0;
+        lo = 0.0;
+        return;
+    }
+    const __int128 v = a.acc;
+    const int64_t top = (int64_t)(v >> 64);
+    const uint64_t bot = (uint64_t)v;
+    // hi: v rounded (the two conversions round separately; the remainder fixes it)
+    double h = (double)top * 18446744073709551616.0 + (double)bot;
+    // exact remainder v - h in 128-bit integers (|h| < 2^127, h has 53 significant bits)
+    int he = 0;
+    const double hm = frexp(h, &he);                 // h = hm * 2^he, 0.5 <= |hm| < 1
+    const int64_t hmi = (int64_t)ldexp(hm, 53);      // exact integer mantissa
+    const int shift = he - 53;
+    const __int128 hv = shift >= 0 ? ((__int128)hmi << shift) : ((__int128)hmi >> (-shift));
+    const __int128 r = v - hv;                       // a few ulps of h
+    const double l = (double)(int64_t)(r >> 32) * 4294967296.0 + (double)(uint32_t)(uint64_t)r;
+    hi = ldexp(h, a.E + scale);
+    lo = ldexp(l, a.E + scale);
+}
+
+}  // namespace permx

@@ -33,6 +33,14 @@ def px():
     return px
 
 
+@pytest.fixture(params=[1, 0], ids=["int_mantissa", "fp64"])
+def arith(request, px):
+    """Run a float64/complex128 test under both walk arithmetics."""
+    old = px.permx_set_fp_arith(request.param)
+    yield request.param
+    px.permx_set_fp_arith(old)
+
+
 def _dev(a, dtype=None):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(a))
@@ -177,7 +185,7 @@ def _check_fp(mats, got):
 
 
 @pytest.mark.parametrize("name", list(ENSEMBLES))
-def test_fp_ensembles_ragged(px, name):
+def test_fp_ensembles_ragged(px, arith, name):
     mats = []
     for n in list(range(1, 19)) + [9, 14]:
         mats.append(ensemble(name, n, 1, seed=2000 + n)[0])
@@ -186,7 +194,7 @@ def test_fp_ensembles_ragged(px, name):
 
 
 @pytest.mark.parametrize("cplx", [True, False])
-def test_fp_larger_sizes(px, cplx):
+def test_fp_larger_sizes(px, arith, cplx):
     # n = 20, 21: relative error against the error bound of float64 products; at
     # these sizes the Haar permanent's terms cancel by ~1e8-1e9, so 1e-9 relative
     # is at the edge of what float64 products can deliver
@@ -197,9 +205,25 @@ def test_fp_larger_sizes(px, cplx):
         ref = O.perm_dp(A)
         _, abs_terms = O.perm_ryser(A, with_abs=True)
         assert abs(v - ref) <= fp_tolerance(ref, abs_terms, A.shape[0]), (A.shape[0], v, ref)
+        if arith == 1:
+            # exact row sums and 62-bit products: 1e-9 relative holds here too
+            assert abs(v - ref) <= 1e-9 * abs(ref), (A.shape[0], v, ref)
 
 
-def test_haar_unitary_n14_one_per_launch(px):
+def test_int_mantissa_relative_at_n22(px):
+    # Haar U(22): float64 products miss 1e-9 relative (measured 1.2e-9); the
+    # integer-mantissa walk must meet it
+    old = px.permx_set_fp_arith(1)
+    try:
+        A = ensemble("haar_u", 22, 1, seed=2100 + 22)[0]
+        v = run_fp(px, [A])[0]
+        ref = O.perm_dp(A)
+        assert abs(v - ref) <= 1e-9 * abs(ref), (v, ref)
+    finally:
+        px.permx_set_fp_arith(old)
+
+
+def test_haar_unitary_n14_one_per_launch(px, arith):
     # 256 Haar-random U(14), seed 0, one matrix per launch
     mats = ensemble("haar_u", 14, 256, seed=0)
     for A in mats[::16]:
@@ -208,7 +232,7 @@ def test_haar_unitary_n14_one_per_launch(px):
         assert abs(v - ref) <= 1e-9 * abs(ref)
 
 
-def test_geodesic_midpoints(px):
+def test_geodesic_midpoints(px, arith):
     # paper §4.1 table: midpoint of the cycle geodesic; even n -> 0
     ns = [5, 7, 9, 11, 13, 15, 17]
     mats = [geodesic_cycle(n, 0.5, "circulant") for n in ns] + [geodesic_cycle(n, 0.5, "principal") for n in ns]
@@ -224,7 +248,7 @@ def test_geodesic_midpoints(px):
     assert np.all(np.abs(even) <= 1e-13)
 
 
-def test_fp_identity_ones_and_hermitian(px):
+def test_fp_identity_ones_and_hermitian(px, arith):
     mats = [np.eye(12, dtype=complex), np.ones((10, 10), complex), np.ones((12, 12))]
     got = run_fp(px, mats[:2])
     assert got[0] == 1.0
@@ -238,7 +262,7 @@ def test_fp_identity_ones_and_hermitian(px):
         assert abs(v.imag) <= fp_tolerance(0.0, abs_terms, 15)
 
 
-def test_fp_alone_equals_in_mix(px):
+def test_fp_alone_equals_in_mix(px, arith):
     # the same matrix alone and inside a ragged batch gives bit-identical results
     A = ensemble("haar_u", 16, 1, seed=77)[0]
     B = ensemble("ginibre_r", 15, 1, seed=78)[0]
@@ -250,7 +274,7 @@ def test_fp_alone_equals_in_mix(px):
     assert mix_r[-1] == alone_r
 
 
-def test_host_variants_match_device(px):
+def test_host_variants_match_device(px, arith):
     mats = [ensemble("haar_u", n, 1, seed=3000 + n)[0] for n in (4, 11, 15)]
     flat, n, off = _pack(mats)
     host = px.perm_c128_host(flat, n, off)
@@ -272,3 +296,62 @@ def test_fp_invalid_arguments(px):
         with pytest.raises(px.PermxError) as e:
             px.perm_f64(A, [n], [0], out)
         assert e.value.code == px.PERMX_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# maximum sizes: closed forms the oracle can evaluate block by block
+# ---------------------------------------------------------------------------
+
+def _block_diag(blocks):
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n), dtype=np.result_type(*blocks))
+    i = 0
+    for b in blocks:
+        k = b.shape[0]
+        M[i:i + k, i:i + k] = b
+        i += k
+    return M
+
+
+def test_fp_max_size_block_diagonal(px, arith):
+    # n = 32 (the float maximum): perm of a block-diagonal matrix is the product of the
+    # blocks' permanents; rows and columns permuted so the blocks interleave
+    g = rng(4000)
+    for cplx in (True, False):
+        blocks = [ensemble("haar_u" if cplx else "haar_o", 8, 1, seed=4000 + 10 * k + cplx)[0] for k in range(4)]
+        M = _block_diag(blocks)
+        P, Q = g.permutation(32), g.permutation(32)
+        M = np.ascontiguousarray(M[P][:, Q])
+        ref = np.prod([O.perm_dp(b) for b in blocks])
+        v = run_fp(px, [M])[0]
+        assert abs(v - ref) <= 1e-9 * abs(ref), (cplx, v, ref)
+
+
+def test_modp_large_block_diagonal(px):
+    # n = 36: product of four 9 x 9 blocks' permanents mod p
+    g = rng(4100)
+    p = 2147483629
+    blocks = [random_residues(9, p, g) for _ in range(4)]
+    M = _block_diag(blocks).astype(np.uint32)
+    P, Q = g.permutation(36), g.permutation(36)
+    M = np.ascontiguousarray(M[P][:, Q])
+    ref = 1
+    for b in blocks:
+        ref = ref * O.perm_modp_brute(b, p) % p
+    assert int(run_modp(px, [M], [p])[0]) == ref
+
+
+def test_modp_n48_gray_window(px):
+    # the F_p maximum n = 48: a sampled window of Gray indices against the oracle
+    g = rng(4200)
+    p = 2147483647
+    A = random_residues(48, p, g)
+    dA = _dev(A.astype(np.int32))
+    for k0 in ((1 << 47) - 300000, (1 << 46) + 12345):
+        assert px.perm_modp_gray_range(dA, 48, p, k0, k0 + 600000) == O.ryser_modp_gray_range(A, p, k0, k0 + 600000)
+
+
+def test_n1_all_fields(px, arith):
+    assert run_fp(px, [np.array([[2.5 - 1j]])])[0] == 2.5 - 1j
+    assert run_fp(px, [np.array([[-3.25]])])[0] == -3.25
+    assert int(run_modp(px, [np.array([[12345]], np.uint32)], [2147483629])[0]) == 12345

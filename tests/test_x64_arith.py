@@ -1,0 +1,138 @@
+"""The integer-mantissa arithmetic of the float64 / complex128 walks, run on
+the CPU through the library's self-test hooks (the same inline functions the
+kernels use) and checked against exact Python integers and fractions."""
+import ctypes
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2602_10141_b300 as px
+    L = px._lib
+    L.permx_x64_mulhi62.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    L.permx_x64_mulhi62.restype = ctypes.c_int64
+    P = ctypes.POINTER
+    L.permx_x64_product.argtypes = [P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int32)]
+    L.permx_x64c_product.argtypes = [P(ctypes.c_int64), P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64),
+                                     P(ctypes.c_int64), P(ctypes.c_int32)]
+    L.permx_x64_accumulate.argtypes = [P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32,
+                                       ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]
+    return L
+
+
+def _arr(v, t=np.int64):
+    a = np.ascontiguousarray(np.array(v, dtype=t))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64 if t == np.int64 else ctypes.c_int32))
+
+
+def test_mulhi62_truncation_bound(lib):
+    rnd = random.Random(1)
+    edge = [0, 1, -1, 2 ** 62, -2 ** 62, 2 ** 61, -(2 ** 61), 2 ** 62 - 1, -(2 ** 62) + 1, 2 ** 31, -(2 ** 31), 12345]
+    cases = [(a, b) for a in edge for b in edge]
+    cases += [(rnd.randint(-2 ** 62, 2 ** 62), rnd.randint(-2 ** 62, 2 ** 62)) for _ in range(20000)]
+    cases += [(rnd.randint(-2 ** 62, 2 ** 62), rnd.randint(-2 ** 40, 2 ** 40)) for _ in range(5000)]
+    for a, b in cases:
+        got = lib.permx_x64_mulhi62(a, b)
+        exact = (a * b) >> 62            # floor
+        assert -2 <= got - exact <= 1, (a, b, got, exact)
+
+
+def _error_scale(R):
+    """sum_i 2^61 prod_{k != i} |R_k|: the size one truncation per factor can reach."""
+    tot = 0
+    for i in range(len(R)):
+        p = 2 ** 61
+        for k, r in enumerate(R):
+            if k != i:
+                p *= abs(r)
+        tot += p
+    return tot
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 12, 23, 32])
+def test_real_product(lib, n):
+    rnd = random.Random(n)
+    for trial in range(300):
+        if trial % 10 == 0:
+            R = [rnd.randint(-2 ** 61 + 1, 2 ** 61 - 1) >> rnd.randint(0, 40) for _ in range(n)]
+        else:
+            R = [rnd.randint(-2 ** 61 + 1, 2 ** 61 - 1) for _ in range(n)]
+        if trial == 5:
+            R[n // 2] = 0
+        a, pa = _arr(R)
+        m, e = ctypes.c_int64(), ctypes.c_int32()
+        assert lib.permx_x64_product(pa, n, ctypes.byref(m), ctypes.byref(e)) == 0
+        exact = 1
+        for r in R:
+            exact *= r
+        got = Fraction(m.value) * Fraction(2) ** e.value
+        assert abs(got - exact) <= Fraction(4 * n, 2 ** 59) * _error_scale(R) + 0, (R, m.value, e.value)
+        if exact == 0:
+            assert m.value == 0
+        else:
+            assert 2 ** 61 <= abs(m.value) <= 2 ** 62
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 11, 26])
+def test_complex_product(lib, n):
+    rnd = random.Random(100 + n)
+    for trial in range(200):
+        Rr = [rnd.randint(-2 ** 60, 2 ** 60) for _ in range(n)]
+        Ri = [rnd.randint(-2 ** 60, 2 ** 60) for _ in range(n)]
+        if trial % 7 == 0:
+            Rr[0] >>= 30
+            Ri[0] >>= 30
+        ar, pr = _arr(Rr)
+        ai, pi = _arr(Ri)
+        re, im, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        assert lib.permx_x64c_product(pr, pi, n, ctypes.byref(re), ctypes.byref(im), ctypes.byref(e)) == 0
+        exact = complex(1, 0)
+        er, ei = 1, 0
+        for x, y in zip(Rr, Ri):
+            er, ei = er * x - ei * y, er * y + ei * x
+        scale = Fraction(2) ** e.value
+        mags = [max(abs(x), abs(y)) * 2 for x, y in zip(Rr, Ri)]   # bound on |R_k|
+        bound = Fraction(16 * n, 2 ** 59) * _error_scale(mags)
+        assert abs(Fraction(re.value) * scale - er) <= bound
+        assert abs(Fraction(im.value) * scale - ei) <= bound
+        assert max(abs(re.value), abs(im.value)) <= 2 ** 61
+
+
+def test_accumulator_exact_sum(lib):
+    rnd = random.Random(7)
+    for trial in range(60):
+        count = rnd.choice([1, 2, 17, 4096])
+        base = rnd.randint(-3000, 3000)
+        m = [rnd.choice([-1, 1]) * rnd.randint(2 ** 61, 2 ** 62) for _ in range(count)]
+        e = [base + rnd.randint(-30, 12) for _ in range(count)]
+        if trial % 5 == 0:                     # a far larger term late in the chunk (rescale path)
+            e[-1] = base + 200
+        neg = [rnd.randint(0, 1) for _ in range(count)]
+        am, pm = _arr(m)
+        ae, pe = _arr(e, np.int32)
+        an, pn = _arr(neg, np.int32)
+        scale = -base
+        hi, lo = ctypes.c_double(), ctypes.c_double()
+        assert lib.permx_x64_accumulate(pm, pe, pn, count, scale, ctypes.byref(hi), ctypes.byref(lo)) == 0
+        exact = sum(Fraction((-1) ** s * mm) * Fraction(2) ** (ee + scale) for mm, ee, s in zip(m, e, neg))
+        tot = sum(Fraction(abs(mm)) * Fraction(2) ** (ee + scale) for mm, ee in zip(m, e))
+        got = Fraction(hi.value) + Fraction(lo.value)
+        # terms may be truncated to the accumulator's grid (2^-24 of the first term's
+        # lowest bit) or, after a rescale, to the larger term's grid
+        assert abs(got - exact) <= tot * Fraction(1, 2 ** 80) + abs(exact) * Fraction(1, 2 ** 100)
+
+
+def test_accumulator_zero_and_tiny(lib):
+    m, pm = _arr([2 ** 61, -(2 ** 61)])
+    e, pe = _arr([0, 0], np.int32)
+    s, ps = _arr([0, 0], np.int32)
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    lib.permx_x64_accumulate(pm, pe, ps, 2, 0, ctypes.byref(hi), ctypes.byref(lo))
+    assert hi.value == 0.0 and lo.value == 0.0
