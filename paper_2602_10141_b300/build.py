@@ -53,14 +53,15 @@ def _gen_dispatch() -> None:
         out += [f"cudaError_t dispatch_{kind}(int n, const {lt}& L, cudaStream_t s) {{",
                 "    const uint64_t items = L.item_end - L.item_begin;",
                 "    if (items == 0) return cudaSuccess;",
-                "    auto grid_for = [&](int bps) {",
-                "        uint64_t want = (items + kRyserThreads - 1) / kRyserThreads;",
+                "    auto grid_for = [&](int bps, int lanes_per_item = 1) {",
+                "        uint64_t want = (items * lanes_per_item + kRyserThreads - 1) / kRyserThreads;",
                 "        uint64_t cap = (uint64_t)sm_count() * (uint64_t)bps;",
                 "        return (int)(want < cap ? want : cap);",
                 "    };",
                 "    switch (n) {"]
         for n in range(1, mx + 1):
-            out.append(f"        case {n}: return launch_{kind}<{n}>(L, grid_for(blocks_per_sm_{kind}<{n}>()), s);")
+            lanes = 2 if (kind == "x64c" and n > 16) else 1   # x64c_paired(n)
+            out.append(f"        case {n}: return launch_{kind}<{n}>(L, grid_for(blocks_per_sm_{kind}<{n}>(), {lanes}), s);")
         out += ["        default: return cudaErrorInvalidValue;", "    }", "}", ""]
     # resident blocks per SM of the kernel that a (kind, n) launch uses
     out += ["int dispatch_blocks_per_sm(int kind, int n) {",

@@ -385,7 +385,7 @@ BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field) {
         g.col_off = col_off;
         g.first_mat = mat_index;
         g.items = (int64_t)g.mats.size() << g.log2_chunks;
-        const int lg = g.log2_chunks >= 5 ? 5 : g.log2_chunks;
+        const int lg = group_log2(g.log2_chunks, chunks_per_warp(g.x64, field == Field::C128, g.n));
         g.partials_per_mat = (int64_t)1 << (g.log2_chunks - lg);
         g.part_off = part_off;
         col_off += g.mat_stride * (int64_t)g.mats.size();

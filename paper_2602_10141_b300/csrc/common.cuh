@@ -118,7 +118,17 @@ cudaError_t dispatch_f64(int n, const FpLaunch& L, cudaStream_t s);
 cudaError_t dispatch_c128(int n, const FpLaunch& L, cudaStream_t s);
 cudaError_t dispatch_x64r(int n, const FpLaunch& L, cudaStream_t s);
 cudaError_t dispatch_x64c(int n, const FpLaunch& L, cudaStream_t s);
-int dispatch_blocks_per_sm(int kind, int n);   // kind: 0 modp, 1 f64, 2 c128, 3 x64 real, 4 x64 complex
+int dispatch_blocks_per_sm(int kind, int n);
+
+// Complex integer-mantissa walks with n > 16 run two lanes per chunk, so a
+// warp covers 16 chunks instead of 32; chunk lane groups (and the partial
+// slots per matrix) follow from this.
+constexpr bool x64c_paired(int n) { return n > 16; }
+inline int chunks_per_warp(bool x64, bool cplx, int n) { return (x64 && cplx && x64c_paired(n)) ? 16 : 32; }
+inline int group_log2(int log2_chunks, int per_warp) {
+    const int w = per_warp == 16 ? 4 : 5;
+    return log2_chunks < w ? log2_chunks : w;
+}   // kind: 0 modp, 1 f64, 2 c128, 3 x64 real, 4 x64 complex
 
 // Arithmetic of the float64 / complex128 walks: 0 = the FP64 pipe (IEEE
 // float64 row sums and products), 1 = integer mantissas (exact fixed-point

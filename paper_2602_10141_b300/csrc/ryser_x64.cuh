@@ -28,8 +28,14 @@ namespace permx {
 // column n = X (Nijenhuis-Wilf offset), each `ld` entries (complex: re, im
 // interleaved per entry), then one word holding -sum_i sigma_i.
 // ---------------------------------------------------------------------------
+// Resident blocks of 256 threads per SM that the register budget targets:
+// two (128 registers per thread) while the row sums and product chains fit
+// without spilling, one beyond.
+template <int N> constexpr int x64r_minb() { return N <= 24 ? 2 : 1; }
+template <int N> constexpr int x64c_minb() { return N <= 16 ? 2 : 1; }
+
 template <int N>
-__global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64r_kernel(const FpLaunch L) {
+__global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kernel(const FpLaunch L) {
     constexpr int NP = pad2(N);
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64r_kernel(const FpLa
 }
 
 template <int N>
-__global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64c_kernel(const FpLaunch L) {
+__global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kernel(const FpLaunch L) {
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
@@ -196,6 +202,123 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_x64c_kernel(const FpLa
     }
 }
 
+// Complex rows wider than 16: two lanes share a chunk.  Lane h of a pair
+// owns rows [h*H, h*H + H) (H = ceil(N/2); the odd lane has N - H rows when
+// N is odd), updates and multiplies only those, and the pair combines its two
+// half products with one shuffle exchange and one more factor, formed in the
+// same operand order on both lanes so both hold the identical term.  Halving
+// the row registers lets two blocks reside per SM.  A warp covers 16 chunks,
+// so lane groups are min(chunks, 16) chunks wide.
+template <int N>
+__global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpLaunch L) {
+    constexpr int H = (N + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int h = lane & 1;
+    const int rows = h ? N - H : H;
+    const int r0 = h * H;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x / 2;
+    const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    const int lg = L.log2_chunks >= 4 ? 4 : L.log2_chunks;
+    const int G = 1 << lg;
+    for (uint64_t base = L.item_begin + ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 2;
+         base < L.item_end; base += stride) {
+        const uint64_t item = base + (lane >> 1);
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        bool valid = item < L.item_end;
+        const double* cold = L.colT;
+        uint64_t c = 0, slot = 0;
+        if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
+        const unsigned pair_mask = __ballot_sync(0xffffffffu, valid);   // both lanes of a pair agree
+        if (valid) {
+            const longlong2* col = reinterpret_cast<const longlong2*>(cold);
+            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            int64_t Rr[H], Ri[H];
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                Rr[i] = 0;
+                Ri[i] = 0;
+                if (i < rows) {
+                    const longlong2 x = __ldg(col + N * N + r0 + i);
+                    Rr[i] = x.x;
+                    Ri[i] = x.y;
+                }
+            }
+            const uint64_t S0 = ks ^ (ks >> 1);
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                if (!((S0 >> j) & 1)) continue;
+#pragma unroll
+                for (int i = 0; i < H; ++i) {
+                    if (i < rows) {
+                        const longlong2 v = __ldg(col + j * N + r0 + i);
+                        Rr[i] += v.x;
+                        Ri[i] += v.y;
+                    }
+                }
+            }
+            const int scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
+            XAcc ar, ai;
+            x64_acc_init(ar);
+            x64_acc_init(ai);
+            for (uint64_t k = ks; k < ke; ++k) {
+                if (k > ks) {
+                    const int j = __ffsll((long long)k) - 1;
+                    const longlong2* cj = col + j * N + r0;
+                    if ((k >> (j + 1)) & 1) {
+#pragma unroll
+                        for (int i = 0; i < H; ++i) {
+                            if (i < rows) {
+                                const longlong2 v = __ldg(cj + i);
+                                Rr[i] -= v.x;
+                                Ri[i] -= v.y;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < H; ++i) {
+                            if (i < rows) {
+                                const longlong2 v = __ldg(cj + i);
+                                Rr[i] += v.x;
+                                Ri[i] += v.y;
+                            }
+                        }
+                    }
+                }
+                // the lane's half product (rows >= 8 here, so all four chains start)
+                XCplx t[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+#pragma unroll
+                for (int i = 4; i < H; ++i)
+                    if (i < rows) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+                XCplx p = x64c_mul(t[0], t[1].re, t[1].im, t[1].e);
+                const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
+                p = x64c_mul(p, p23.re, p23.im, p23.e);
+                // exchange halves; both lanes multiply (lane 0's half) x (lane 1's half)
+                XCplx o;
+                o.re = (int64_t)__shfl_xor_sync(pair_mask, (long long)p.re, 1);
+                o.im = (int64_t)__shfl_xor_sync(pair_mask, (long long)p.im, 1);
+                o.e = __shfl_xor_sync(pair_mask, p.e, 1);
+                const XCplx a = h ? o : p, b = h ? p : o;
+                const XCplx t2 = x64c_mul(a, b.re, b.im, b.e);
+                x64_acc_add(ar, t2.re, t2.e, k & 1);
+                x64_acc_add(ai, t2.im, t2.e, k & 1);
+            }
+            if (!h) {
+                x64_acc_to_dd(ar, scale, sr, cr);
+                x64_acc_to_dd(ai, scale, si, ci);
+            }
+        }
+        group_reduce(sr, cr, 2 * G);
+        group_reduce(si, ci, 2 * G);
+        if ((lane & (2 * G - 1)) == 0 && valid) {
+            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
+            out[0] = make_double2(sr, cr);
+            out[1] = make_double2(si, ci);
+        }
+    }
+}
+
 template <int N>
 cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s) {
     ryser_x64r_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
@@ -203,7 +326,8 @@ cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s) {
 }
 template <int N>
 cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s) {
-    ryser_x64c_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+    if constexpr (x64c_paired(N)) ryser_x64c2_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+    else ryser_x64c_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 template <int N>
@@ -222,8 +346,12 @@ int blocks_per_sm_x64c() {
     static int cached = -1;
     if (cached < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
+        cudaError_t e;
+        if constexpr (x64c_paired(N))
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c2_kernel<N>, kRyserThreads, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c_kernel<N>, kRyserThreads, 0);
+        if (e != cudaSuccess || b < 1) b = 1;
         cached = b;
     }
     return cached;

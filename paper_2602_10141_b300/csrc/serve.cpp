@@ -181,10 +181,10 @@ void plan_request(Request* r, bool x64) {
     const int bits = walk_bits(r->n, 1);
     r->ell = chunk_log2((Field)r->field, r->n, bits);
     r->log2_chunks = bits - r->ell;
-    r->lg = r->log2_chunks >= 5 ? 5 : r->log2_chunks;
+    r->x64 = !modp && x64;
+    r->lg = group_log2(r->log2_chunks, chunks_per_warp(r->x64, r->field == PERMX_FIELD_C128, r->n));
     r->chunks = 1ull << r->log2_chunks;
     r->ld = modp ? pad4(r->n) : r->field == PERMX_FIELD_F64 ? pad2(r->n) : r->n;
-    r->x64 = !modp && x64;
     // staged columns (plus the x column); the integer-mantissa layout adds a scale word pair
     r->col_bytes = align256((size_t)(r->n + 1) * r->ld * entry_bytes(r->field) + (r->x64 ? 16 : 0));
     const size_t tail = modp ? 8 : (size_t)(r->chunks >> r->lg) * (r->field == PERMX_FIELD_C128 ? 32 : 16);

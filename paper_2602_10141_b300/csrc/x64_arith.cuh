@@ -39,34 +39,59 @@ __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
     return hh * 4 + (mid >> 30);
 }
 
-// Left shift that puts the top bit of |x| at position T-1, i.e. |x| in
-// [2^(T-1), 2^T] (0 stays 0); mag_or is |x| (or an OR of several |.|).
-template <int T>
-__host__ __device__ __forceinline__ int x64_norm_shift(uint64_t mag_or) {
-    const int lz = x64_clz(mag_or | 1ull);
-    const int s = lz - (64 - T);
-    return s > 0 ? s : 0;
+// Normalisation works on the high 32-bit word only: |x| is at most 2^62, so
+// the top bit of a non-tiny value is in the high word, a 32-bit clz finds it
+// and the shift stays below 32 (two funnel-shift instructions).  A value whose
+// high word is zero (|x| < 2^32, only when a row sum is tiny) is shifted by
+// the largest such amount and stays partly normalised: its term is tiny and
+// its absolute error is still bounded by the scale of typical terms.
+__host__ __device__ __forceinline__ uint32_t x64_hiword(int64_t x) { return (uint32_t)((uint64_t)x >> 32); }
+__host__ __device__ __forceinline__ uint32_t x64_mag_hi(int64_t x) {
+    const uint32_t h = x64_hiword(x);
+    return h ^ (uint32_t)((int32_t)h >> 31);   // |x| >> 32 (one less for negative x)
 }
-__host__ __device__ __forceinline__ uint64_t x64_mag(int64_t x) { return (uint64_t)(x ^ (x >> 63)); }
+__host__ __device__ __forceinline__ int x64_clz32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __clz((int)v);
+#else
+    return v ? __builtin_clz(v) : 32;
+#endif
+}
+// Shift that puts the top bit of max |x| at position T-1 (T >= 33), in [0, 31].
+template <int T>
+__host__ __device__ __forceinline__ int x64_norm_shift_hi(uint32_t mag_hi_or) {
+    const int s = x64_clz32(mag_hi_or) - (64 - T);
+    return s < 0 ? 0 : (s > 31 ? 31 : s);
+}
+// x << s for 0 <= s <= 31, as two 32-bit word operations
+__host__ __device__ __forceinline__ int64_t x64_shl(int64_t x, int s) {
+    const uint32_t lo = (uint32_t)(uint64_t)x, hi = x64_hiword(x);
+#ifdef __CUDA_ARCH__
+    const uint32_t nhi = __funnelshift_l(lo, hi, s);
+#else
+    const uint32_t nhi = s ? (hi << s) | (lo >> (32 - s)) : hi;
+#endif
+    return (int64_t)(((uint64_t)nhi << 32) | (uint32_t)(lo << s));
+}
 
 struct XReal { int64_t m; int e; };
 struct XCplx { int64_t re, im; int e; };
 
 // real: mantissa target |m| in [2^61, 2^62]
 __host__ __device__ __forceinline__ XReal x64_from_int(int64_t r) {
-    const int s = x64_norm_shift<62>(x64_mag(r));
-    return XReal{r << s, -s};
+    const int s = x64_norm_shift_hi<62>(x64_mag_hi(r));
+    return XReal{x64_shl(r, s), -s};
 }
 __host__ __device__ __forceinline__ XReal x64_mul(XReal a, int64_t m2, int e2) {
     const int64_t x = x64_mulhi62(a.m, m2);
-    const int s = x64_norm_shift<62>(x64_mag(x));
-    return XReal{x << s, a.e + e2 + 62 - s};
+    const int s = x64_norm_shift_hi<62>(x64_mag_hi(x));
+    return XReal{x64_shl(x, s), a.e + e2 + 62 - s};
 }
 
 // complex: larger component target in [2^60, 2^61] (sums of two stay below 2^62)
 __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) {
-    const int s = x64_norm_shift<61>(x64_mag(re) | x64_mag(im));
-    return XCplx{re << s, im << s, -s};
+    const int s = x64_norm_shift_hi<61>(x64_mag_hi(re) | x64_mag_hi(im));
+    return XCplx{x64_shl(re, s), x64_shl(im, s), -s};
 }
 // (a.re + i a.im) * (br + i bi), |br|, |bi| <= 2^61; three products (Karatsuba)
 __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t bi, int eb) {
@@ -74,8 +99,8 @@ __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t 
     const int64_t k2 = x64_mulhi62(a.re, bi - br);
     const int64_t k3 = x64_mulhi62(a.im, br + bi);
     const int64_t re = k1 - k3, im = k1 + k2;
-    const int s = x64_norm_shift<61>(x64_mag(re) | x64_mag(im));
-    return XCplx{re << s, im << s, a.e + eb + 62 - s};
+    const int s = x64_norm_shift_hi<61>(x64_mag_hi(re) | x64_mag_hi(im));
+    return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
 }
 
 // Exact fixed-point sum of one chunk's terms: value = acc * 2^E.  The first
