@@ -133,7 +133,8 @@ def cpu_baseline(primes, mats, target_s: float = 12.0):
     import oracle as O
     A, p = mats[0], primes[0]
     k0 = 1 << 31
-    span = 1 << 16
+    O.ryser_modp_gray_range(A, p, k0, k0 + (1 << 12))   # start the OpenMP threads
+    span = 1 << 19
     t0 = time.perf_counter()
     O.ryser_modp_gray_range(A, p, k0, k0 + span)
     dt = time.perf_counter() - t0
@@ -153,11 +154,12 @@ def run_reference(args, rank, world):
     import oracle as O
     primes = O.primes_1_mod_n(N, NPRIMES)
     mats = [O.schur_residue_matrix(N, p, O.primitive_nth_root(p, N)) for p in primes]
-    # calibrate a per-step sample of about 2-4 s
+    # calibrate a per-step sample of about 3 s
     k0 = 1 << 31
+    O.ryser_modp_gray_range(mats[0], primes[0], k0, k0 + (1 << 12))   # start the OpenMP threads
     t0 = time.perf_counter()
-    O.ryser_modp_gray_range(mats[0], primes[0], k0, k0 + (1 << 16))
-    rate = (1 << 16) / max(time.perf_counter() - t0, 1e-9)
+    O.ryser_modp_gray_range(mats[0], primes[0], k0, k0 + (1 << 19))
+    rate = (1 << 19) / max(time.perf_counter() - t0, 1e-9)
     span = int(min(max(rate * 3.0, 1 << 16), 1 << 30))
     for w in range(args.warmup):
         O.ryser_modp_gray_range(mats[w % NPRIMES], primes[w % NPRIMES], k0, k0 + (1 << 14))
@@ -171,7 +173,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "primes": primes},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "primes": NPRIMES, "prime_list": primes},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{span} Gray indices of S_33 per step (bounded sample; the full "
                                        f"step is {NPRIMES} x 2^33 subsets)"},
@@ -314,7 +316,7 @@ def main():
             "clocks": cs,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
                     "d2h_bytes_per_step": 4 * NPRIMES},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 4 * args.steps,   # metadata, staging, Gray walk, finalize per step
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(primes, mats)

@@ -48,11 +48,15 @@ int chunk_log2(Field field, int n, int bits) {
 }
 
 int chunk_log2_fp(int bits) {
-    // At most 2^10 steps per chunk: the float64 walk's row-sum drift grows like
-    // sqrt(L) ulps, and a chunk is the unit of work a serving step cannot split;
-    // at least 2^6 (or the whole walk) so the O(n^2) chunk start stays small.
-    int ell = bits - 14;
-    int lo = bits < 6 ? bits : 6;
+    // About 2^10 chunks per matrix so that even one small matrix spreads over
+    // many threads (a chunk's steps run serially, so its length sets the
+    // latency of a lone small matrix); at most 2^10 steps per chunk (the
+    // float64 walk's row-sum drift grows like sqrt(L) ulps, and a chunk is the
+    // unit of work a serving step cannot split); at least 2^3 steps (or the
+    // whole walk), where the O(n^2) chunk start is still small next to the n
+    // products per step.
+    int ell = bits - 10;
+    int lo = bits < 3 ? bits : 3;
     if (ell < lo) ell = lo;
     if (ell > 10) ell = 10;
     return ell;
@@ -417,6 +421,35 @@ static int alloc_ws(Workspace& ws, size_t bytes, cudaStream_t s) {
     return PERMX_OK;
 }
 
+// Metadata of small batches travels as a kernel parameter (by value) and is
+// written into the workspace on the device: the call then stays fully
+// asynchronous, where a copy from pageable host memory would synchronise the
+// stream first.
+template <int SZ>
+struct MetaBytes {
+    uint32_t words;
+    uint32_t w[SZ / 4];
+};
+template <int SZ>
+__global__ void meta_copy_kernel(const MetaBytes<SZ> m, uint32_t* __restrict__ dst) {
+    for (uint32_t i = threadIdx.x; i < m.words; i += blockDim.x) dst[i] = m.w[i];
+}
+template <int SZ>
+static cudaError_t meta_copy(const std::vector<unsigned char>& host, void* dst, cudaStream_t s) {
+    MetaBytes<SZ> m;
+    m.words = (uint32_t)((host.size() + 3) / 4);
+    std::memset(m.w, 0, sizeof m.w);
+    std::memcpy(m.w, host.data(), host.size());
+    meta_copy_kernel<SZ><<<1, 256, 0, s>>>(m, static_cast<uint32_t*>(dst));
+    return cudaGetLastError();
+}
+static cudaError_t upload_meta(const std::vector<unsigned char>& host, void* dst, cudaStream_t s) {
+    if (host.size() <= 1024) return meta_copy<1024>(host, dst, s);
+    if (host.size() <= 4096) return meta_copy<4096>(host, dst, s);
+    if (host.size() <= 16384) return meta_copy<16384>(host, dst, s);
+    return cudaMemcpyAsync(dst, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+}
+
 // ---------------------------------------------------------------------------
 // prepare / execute / release.  prepare() plans the batch, allocates one
 // workspace and uploads the metadata; execute() only enqueues kernels and a
@@ -493,7 +526,7 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
     int rc = alloc_ws(ws, X.bytes, s);
     if (rc) return rc;
     X.ws = static_cast<unsigned char*>(ws.base);
-    cudaError_t e = cudaMemcpyAsync(X.ws, host.data(), X.o_meta_end, cudaMemcpyHostToDevice, s);
+    cudaError_t e = upload_meta(host, X.ws, s);
     if (e != cudaSuccess) {
         release_batch(X, s);
         return cuda_fail(e, "metadata upload");

@@ -26,12 +26,14 @@ __device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p) 
     uint32_t d = r - a;           // wraps to > 2^31 > p when r < a
     return min(d, d + p);
 }
+// (-p, p) -> [0, p): a negative value wraps above p, so the unsigned min picks r + p
+__device__ __forceinline__ uint32_t mont_fix(uint32_t r, uint32_t p) { return min(r, r + p); }
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
     uint64_t T = (uint64_t)a * b;
     uint32_t m = (uint32_t)T * pinv;
     uint32_t mh = __umulhi(m, p);
     uint32_t r = (uint32_t)(T >> 32) - mh;   // true value in (-p, p)
-    return min(r, r + p);
+    return mont_fix(r, p);
 }
 
 // prod_i r_i * R^{-(N-1)} by a balanced tree (depth log2 N) for ILP.  The
