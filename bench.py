@@ -41,6 +41,9 @@ NPRIMES = 5
 METRIC = "ryser_terms_per_s"
 UNIT = "terms/s"
 WORKLOAD = "schur_n33_fp_5primes"
+# dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch of this
+# command, from a one-pass ncu capture at full size (kernel unchanged since)
+WALK_DRAM_BYTES_PER_LAUNCH = 983698
 
 
 def _rank_env():
@@ -207,6 +210,9 @@ def main():
                     choices=["schur33", "haar14_plain", "ensembles_batched", "serving", "profile_fp", "schur_long"],
                     help="schur33 is the headline; the others measure the plain, batched and served paths")
     ap.add_argument("--ns", default="", help="schur_long: comma-separated n (default 36..43)")
+    ap.add_argument("--ckpt-dir", default="", help="schur_long: keep checkpoints here (resume from them)")
+    ap.add_argument("--max-slices", type=int, default=0,
+                    help="schur_long: stop after this many checkpointed slices per n (0 = run to the end)")
     ap.add_argument("--scale", type=float, default=0.02,
                     help="ensembles_batched / serving: fraction of the full sample counts")
     args = ap.parse_args()
@@ -310,7 +316,8 @@ def main():
             "perms_per_s": NPRIMES * args.steps * world / t_max,
             "terms_evaluated_per_s": evaluated_per_step * args.steps * world / t_max,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tterms/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": WALK_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_unit": "bytes per launch",
                          "kernel": f"ryser_modp_kernel<{N}>",
                          "peak_source": "IMAD-pipe bound from measured per-instruction rates x sampled SM clock"},
             "clocks": cs,

@@ -55,22 +55,38 @@ def run(args):
 
 
 def schur_long(args):
-    """Exact perm(S_n) for n = 36..43 (5 primes below 2^31 + 1 check prime each),
-    sliced into checkpointed kernel launches; one JSON line per n."""
+    """Exact perm(S_n) for n = 36..43 by default (any n <= 48 with --ns; 5 or 6
+    primes below 2^31 + 1 check prime each), sliced into checkpointed kernel
+    launches; one JSON line per n.  With --ckpt-dir and --max-slices a long n
+    runs over several invocations, each resuming from the checkpoint."""
     import tempfile
 
     import paper_2602_10141_b300 as px
     ns = [int(x) for x in args.ns.split(",")] if args.ns else list(range(36, 44))
-    tmp = tempfile.mkdtemp(prefix="permx_schur_")
+    tmp = args.ckpt_dir or tempfile.mkdtemp(prefix="permx_schur_")
+    os.makedirs(tmp, exist_ok=True)
     for n in ns:
         ck = os.path.join(tmp, f"s{n}.ckpt")
+        resumed = os.path.exists(ck)
         t0 = time.perf_counter()
-        value, primes, residues = px.perm_schur_crt_ex(n, 0, ck)
+        try:
+            value, primes, residues = px.perm_schur_crt_ex(n, 0, ck, max_slices=args.max_slices)
+        except px.PermxError as e:
+            if e.code != px.PERMX_EAGAIN:
+                raise
+            with open(ck) as f:
+                state = f.read().split("\n")
+            print(json.dumps({"workload": "schur_long", "n": n, "stopped": True, "seconds": time.perf_counter() - t0,
+                              "slices": args.max_slices, "checkpoint": ck,
+                              "state": [ln for ln in state if ln.startswith(("done", "cursor"))]}), flush=True)
+            continue
         dt = time.perf_counter() - t0
         terms = len(primes) * n * 2.0 ** (n - 1)
         print(json.dumps({"workload": "schur_long", "n": n, "perm_S_n": str(value), "seconds": dt,
                           "primes": primes, "residues": residues, "check_prime": primes[-1],
-                          "evaluated_terms_per_s": terms / dt, "nominal_terms_per_s": 2 * terms / dt,
+                          "resumed": resumed,   # seconds and rates then cover this call's share only
+                          "evaluated_terms_per_s": None if resumed else terms / dt,
+                          "nominal_terms_per_s": None if resumed else 2 * terms / dt,
                           "bound_ok": value * value <= n ** n}), flush=True)
     return 0
 

@@ -174,10 +174,13 @@ int perm_plan_destroy(perm_plan* plan);
  * chunk length of a matrix is 2^ell Gray steps with ell a function of
  * (field, n) only, so results do not depend on batch composition; float
  * results do depend on ell (rounding), F_p results never.  perm_tune_set
- * pins ell for (field, n) (0 restores the built-in rule); perm_tune_get
+ * pins ell for (field, n) (0 restores the built-in rule; ell <= 40 for F_p,
+ * ell <= PERMX_MAX_ELL_FP for the float fields, whose exact 128-bit chunk
+ * accumulator needs the headroom; EINVAL otherwise); perm_tune_get
  * returns the ell in force; perm_autotune times ell0-3 .. ell0+3 around the
  * built-in rule on a synthetic batch of `batch` n x n matrices (`reps`
  * timed passes each), keeps the fastest in the table and returns it. */
+#define PERMX_MAX_ELL_FP 16
 int perm_tune_set(int field, int32_t n, int32_t ell);
 int perm_tune_get(int field, int32_t n);
 int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* best_ell);

@@ -30,6 +30,14 @@ int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t*
 int permx_x64_accumulate(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count, int32_t scale,
                          double* hi, double* lo);
 
+/* The same sum split into `parts` consecutive runs (parts a power of two,
+ * <= 32), one accumulator per run, merged as the kernels merge the lanes of
+ * a group (xor butterfly of symmetric merges), then returned as above.  With
+ * swap != 0 every merge takes its operands in the other order; the bits must
+ * not change. */
+int permx_x64_accumulate_merged(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count,
+                                int32_t parts, int32_t swap, int32_t scale, double* hi, double* lo);
+
 #ifdef __cplusplus
 }
 #endif

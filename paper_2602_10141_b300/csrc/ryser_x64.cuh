@@ -23,6 +23,23 @@
 
 namespace permx {
 
+// Exact reduction of the lanes' chunk accumulators over aligned groups of
+// `lanes` lanes (xor butterfly of symmetric merges), in integers: the
+// double-double conversion then happens once per group instead of once per
+// chunk, which keeps the slow FP64 pipe out of the per-chunk path.
+__device__ __forceinline__ void x64_group_merge(XAcc& a, int lanes) {
+    for (int d = 1; d < lanes; d <<= 1) {
+        XAcc b;
+        const uint64_t lo = (uint64_t)a.acc, hi = (uint64_t)(a.acc >> 64);
+        const uint64_t blo = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo, d);
+        const uint64_t bhi = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)hi, d);
+        b.acc = (__int128)(((unsigned __int128)bhi << 64) | blo);
+        b.E = __shfl_xor_sync(0xffffffffu, a.E, d);
+        b.set = __shfl_xor_sync(0xffffffffu, (int)a.set, d) != 0;
+        x64_acc_merge(a, b);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // kernels.  Staged layout per matrix (int64 words): columns 0..n-1 of A,
 // column n = X (Nijenhuis-Wilf offset), each `ld` entries (complex: re, im
@@ -49,6 +66,9 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
+        XAcc acc;
+        x64_acc_init(acc);
+        int scale = 0;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const int64_t* col = reinterpret_cast<const int64_t*>(cold);
@@ -68,9 +88,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
                     if (2 * q + 1 < N) R[2 * q + 1] += v.y;
                 }
             }
-            const int scale = (int)col[(N + 1) * NP];
-            XAcc acc;
-            x64_acc_init(acc);
+            scale = (int)col[(N + 1) * NP];
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -107,10 +125,12 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
                 }
                 x64_acc_add(acc, p.m, p.e, k & 1);
             }
-            x64_acc_to_dd(acc, scale, s, comp);
         }
-        group_reduce(s, comp, G);
-        if ((lane & (G - 1)) == 0 && valid) reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
+        x64_group_merge(acc, G);
+        if ((lane & (G - 1)) == 0 && valid) {
+            x64_acc_to_dd(acc, scale, s, comp);
+            reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
+        }
     }
 }
 
@@ -128,6 +148,10 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
+        XAcc ar, ai;
+        x64_acc_init(ar);
+        x64_acc_init(ai);
+        int scale = 0;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const longlong2* col = reinterpret_cast<const longlong2*>(cold);
@@ -150,10 +174,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
                     Ri[i] += v.y;
                 }
             }
-            const int scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
-            XAcc ar, ai;
-            x64_acc_init(ar);
-            x64_acc_init(ai);
+            scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -189,12 +210,12 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
                 x64_acc_add(ar, p.re, p.e, k & 1);
                 x64_acc_add(ai, p.im, p.e, k & 1);
             }
+        }
+        x64_group_merge(ar, G);
+        x64_group_merge(ai, G);
+        if ((lane & (G - 1)) == 0 && valid) {
             x64_acc_to_dd(ar, scale, sr, cr);
             x64_acc_to_dd(ai, scale, si, ci);
-        }
-        group_reduce(sr, cr, G);
-        group_reduce(si, ci, G);
-        if ((lane & (G - 1)) == 0 && valid) {
             double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
             out[0] = make_double2(sr, cr);
             out[1] = make_double2(si, ci);
@@ -227,6 +248,10 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
+        XAcc ar, ai;
+        x64_acc_init(ar);
+        x64_acc_init(ai);
+        int scale = 0;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         const unsigned pair_mask = __ballot_sync(0xffffffffu, valid);   // both lanes of a pair agree
         if (valid) {
@@ -256,10 +281,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                     }
                 }
             }
-            const int scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
-            XAcc ar, ai;
-            x64_acc_init(ar);
-            x64_acc_init(ai);
+            scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -304,14 +326,16 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 x64_acc_add(ar, t2.re, t2.e, k & 1);
                 x64_acc_add(ai, t2.im, t2.e, k & 1);
             }
-            if (!h) {
-                x64_acc_to_dd(ar, scale, sr, cr);
-                x64_acc_to_dd(ai, scale, si, ci);
-            }
         }
-        group_reduce(sr, cr, 2 * G);
-        group_reduce(si, ci, 2 * G);
+        if (h) {                 // the odd lane holds the same sums: count them once
+            x64_acc_init(ar);
+            x64_acc_init(ai);
+        }
+        x64_group_merge(ar, 2 * G);
+        x64_group_merge(ai, 2 * G);
         if ((lane & (2 * G - 1)) == 0 && valid) {
+            x64_acc_to_dd(ar, scale, sr, cr);
+            x64_acc_to_dd(ai, scale, si, ci);
             double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
             out[0] = make_double2(sr, cr);
             out[1] = make_double2(si, ci);

@@ -57,4 +57,30 @@ int permx_x64_accumulate(const int64_t* m, const int32_t* e, const int32_t* neg,
     return 0;
 }
 
+int permx_x64_accumulate_merged(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count,
+                                int32_t parts, int32_t swap, int32_t scale, double* hi, double* lo) {
+    if (!m || !e || !neg || !hi || !lo || count < 0 || count > 4096 || parts < 1 || parts > 32 ||
+        (parts & (parts - 1)))
+        return -1;
+    XAcc a[32];
+    const int per = (count + parts - 1) / parts;
+    for (int q = 0; q < parts; ++q) {
+        x64_acc_init(a[q]);
+        for (int k = q * per; k < count && k < (q + 1) * per; ++k) x64_acc_add(a[q], m[k], e[k], neg[k] != 0);
+    }
+    // every "lane" q merges with q ^ d, as the warp butterfly does
+    for (int d = 1; d < parts; d <<= 1) {
+        XAcc b[32];
+        for (int q = 0; q < parts; ++q) {
+            b[q] = swap ? a[q ^ d] : a[q];
+            x64_acc_merge(b[q], swap ? a[q] : a[q ^ d]);
+        }
+        for (int q = 0; q < parts; ++q) a[q] = b[q];
+    }
+    for (int q = 1; q < parts; ++q)
+        if (a[q].set != a[0].set || (a[0].set && (a[q].acc != a[0].acc || a[q].E != a[0].E))) return -2;
+    x64_acc_to_dd(a[0], scale, *hi, *lo);
+    return 0;
+}
+
 }  // extern "C"

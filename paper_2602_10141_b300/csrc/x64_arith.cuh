@@ -136,6 +136,26 @@ __host__ __device__ __forceinline__ void x64_acc_add(XAcc& a, int64_t m, int e, 
     else return;
     a.acc = negate ? a.acc - v : a.acc + v;
 }
+// a <- a + b, both aligned to the larger exponent (the smaller-exponent one
+// is shifted right).  The operation is symmetric in a and b, so a fixed
+// butterfly of merges gives the same bits on every lane and in every batch.
+// A term is below 2^102 on its accumulator's grid (mantissa < 2^62, shift
+// <= 40), a chunk of at most 2^16 terms below 2^118, and 32 merges keep the
+// sum below 2^123.
+__host__ __device__ __forceinline__ __int128 x64_sar128(__int128 v, int d) {
+    return d <= 0 ? v : (d < 127 ? (v >> d) : (v < 0 ? (__int128)-1 : (__int128)0));
+}
+__host__ __device__ __forceinline__ void x64_acc_merge(XAcc& a, const XAcc& b) {
+    if (!b.set) return;
+    if (!a.set) {
+        a = b;
+        return;
+    }
+    const int E = a.E > b.E ? a.E : b.E;
+    a.acc = x64_sar128(a.acc, E - a.E) + x64_sar128(b.acc, E - b.E);
+    a.E = E;
+}
+
 // acc * 2^(E + scale) as a double-double (hi + lo)
 __host__ __device__ __forceinline__ void x64_acc_to_dd(const XAcc& a, int scale, double& hi, double& lo) {
     if (!a.set || a.acc == 0) {

@@ -141,3 +141,34 @@ def test_accumulator_zero_and_tiny(lib):
     hi, lo = ctypes.c_double(), ctypes.c_double()
     lib.permx_x64_accumulate(pm, pe, ps, 2, 0, ctypes.byref(hi), ctypes.byref(lo))
     assert hi.value == 0.0 and lo.value == 0.0
+
+
+@pytest.mark.parametrize("parts", [1, 2, 4, 32])
+def test_accumulator_merge_exact_and_symmetric(lib, parts):
+    """Lane accumulators merged by the group butterfly: every lane ends with
+    the same bits, the operand order of a merge does not matter, and the
+    result is the exact sum up to the larger grid's truncation."""
+    f = lib.permx_x64_accumulate_merged
+    P = ctypes.POINTER
+    f.argtypes = [P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
+                  ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]
+    rnd = random.Random(40 + parts)
+    for trial in range(40):
+        count = rnd.choice([parts, 3 * parts + 1, 1024])
+        base = rnd.randint(-2000, 2000)
+        m = [rnd.choice([-1, 1]) * rnd.randint(2 ** 61, 2 ** 62) for _ in range(count)]
+        e = [base + rnd.randint(-60, 60) for _ in range(count)]   # lanes start at very different grids
+        neg = [rnd.randint(0, 1) for _ in range(count)]
+        am, pm = _arr(m)
+        ae, pe = _arr(e, np.int32)
+        an, pn = _arr(neg, np.int32)
+        outs = []
+        for swap in (0, 1):
+            hi, lo = ctypes.c_double(), ctypes.c_double()
+            assert f(pm, pe, pn, count, parts, swap, -base, ctypes.byref(hi), ctypes.byref(lo)) == 0
+            outs.append((hi.value, lo.value))
+        assert outs[0] == outs[1]
+        exact = sum(Fraction((-1) ** s * mm) * Fraction(2) ** (ee - base) for mm, ee, s in zip(m, e, neg))
+        tot = sum(Fraction(abs(mm)) * Fraction(2) ** (ee - base) for mm, ee in zip(m, e))
+        got = Fraction(outs[0][0]) + Fraction(outs[0][1])
+        assert abs(got - exact) <= tot * Fraction(1, 2 ** 70) + abs(exact) * Fraction(1, 2 ** 100)
