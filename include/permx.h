@@ -122,6 +122,24 @@ int perm_f64_host(const double* A, const int32_t* n, const int64_t* offset, int6
 int perm_modp_host(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
                    int64_t batch, uint32_t* out, void* stream);
 
+/* Permanents of submatrices (paper §8, boson sampling: the amplitude of n
+ * photons entering modes c_1..c_n and leaving modes r_1..r_n of an
+ * interferometer U is perm(U_T); with repeated modes the probability is
+ * |perm(U_T)|^2 / (prod_i s_i! prod_j t_j!), s and t the occupation numbers).
+ *   out[b] = perm( U[rows[b*n + i], cols[b*n + j]] )_{i,j < n}
+ * U: DEVICE m x m matrix, row-major with row stride ldu >= m entries
+ * (complex128: 16-byte aligned).  rows, cols: HOST arrays of batch*n
+ * indices in [0, m), repeats allowed; checked before anything is enqueued
+ * (EINVAL names the first bad index).  out: DEVICE array of batch values.
+ * 1 <= n <= PERMX_MAX_N_FP, m >= 1 (n may exceed m when modes repeat).
+ * Asynchronous on `stream` after the host checks (the index arrays are
+ * copied during the call).  Each result has the bits perm_c128 / perm_f64
+ * gives for the extracted n x n matrix.  Errors: EINVAL, ENOMEM, ECUDA. */
+int perm_c128_gather(const perm_c128_t* U, int32_t m, int64_t ldu, const int32_t* rows, const int32_t* cols,
+                     int32_t n, int64_t batch, perm_c128_t* out, void* stream);
+int perm_f64_gather(const double* U, int32_t m, int64_t ldu, const int32_t* rows, const int32_t* cols, int32_t n,
+                    int64_t batch, double* out, void* stream);
+
 /* Allocation-free variant of perm_modp (the paper has no counterpart; this is
  * an interface for callers that cannot allocate memory during a call, e.g.
  * because another allocator owns the device memory budget or because the
@@ -276,6 +294,44 @@ int serve_drain(perm_server* h, int64_t timeout_ms);
 /* Counters: submitted, completed, resident, steps, launches (host array of 5). */
 int serve_stats(perm_server* h, int64_t* stats5);
 int serve_destroy(perm_server* h);
+
+/* ------------------------------------------------------------------------
+ * Sample statistics of a batch of permanents, on the device (the
+ * distributional measurements of paper §4 (Haar unitary: E|perm|^2,
+ * circularity), §5 Table "orthogonal" (variance and excess kurtosis of
+ * perm(O)), §6 (real-valuedness of Hermitian permanents), §7 Table
+ * "lognormal" (skewness and excess kurtosis of log|perm|) and the
+ * anti-concentration probabilities Pr[|perm|^2 >= threshold]).
+ *
+ * values: `count` device values, complex128 (field PERMX_FIELD_C128,
+ * 16-byte aligned) or float64 (PERMX_FIELD_F64, imaginary part 0).
+ * out: ONE perm_stats_t in DEVICE memory (8-byte aligned), written by the
+ * last kernel; ready after `stream` is synchronised.  Moments are the
+ * plain (biased, divide by count) sample moments; central moments come from
+ * a second pass about the first pass's means.  With |z|^2 := rn(rn(re*re) +
+ * rn(im*im)) and |z| := sqrt(|z|^2) (correctly rounded, no fused multiply-
+ * add):
+ *   count_nonzero  samples with |z|^2 > 0 (the log moments use only these,
+ *                  with log|z| := log(|z|^2) / 2; NaN when there are none)
+ *   count_above    samples with |z|^2 >= threshold
+ *   count_real     samples with |Im z| <= real_tol * |z| (every sample of a
+ *                  float64 input)
+ * skew = m3 / m2^1.5 and excess kurtosis = m4 / m2^2 - 3 (NaN when m2 = 0).
+ * Deterministic: the reduction order depends on count only.  Errors: EINVAL
+ * (field MODP, count < 1, NULL or misaligned pointer, real_tol < 0 or NaN),
+ * ENOMEM, ECUDA.  Workspace comes from the library pool (stream-ordered). */
+typedef struct {
+    int64_t count, count_nonzero, count_above, count_real;
+    double mean_re, mean_im;
+    double var_re, var_im, cov_re_im;   /* central second moments */
+    double skew_re, exkurt_re;          /* of Re z */
+    double mean_abs2, mean_abs4;        /* E|z|^2, E|z|^4 */
+    double mean_z2_re, mean_z2_im;      /* E[z^2] (pseudo-covariance about 0) */
+    double min_abs2, max_abs2;
+    double log_mean, log_var, log_skew, log_exkurt;   /* of log|z| over nonzero samples */
+} perm_stats_t;
+int perm_sample_stats(int field, const void* values, int64_t count, double threshold, double real_tol,
+                      perm_stats_t* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,12 @@ What it computes, and where the paper defines it:
   ``c_m = #{sigma : sum_i i*sigma(i) = m (mod n)}`` reduced modulo the
   cyclotomic polynomial ``Phi_n`` (definition of ``S_n``, paper §1).
 
+* ``sample_stats`` — the sample moments, counts and extremes the paper
+  reports over batches of permanents (§4 second moment and circularity, §5
+  Table "orthogonal", §6 real-valuedness, §7 Table "lognormal", the
+  anti-concentration probabilities), from their textbook definitions with
+  exactly rounded sums (``math.fsum``) in two passes.
+
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself: brute force, closed forms, invariants and the paper's printed
 midpoint table (Table "midpoint", §4.1).
@@ -432,3 +438,57 @@ def schur_exact(n: int) -> int:
 def schur_modp_from_counts(n: int, p: int, g: int) -> int:
     """perm((g^{jk}) mod p) = sum_m c_m g^m mod p."""
     return sum(c * pow(g, m, p) for m, c in enumerate(schur_counts(n))) % p
+
+
+def sample_stats(values, threshold: float = math.inf, real_tol: float = 0.0) -> dict:
+    """Sample statistics of a list of permanents (paper §4-§7).
+
+    Plain (biased, divide-by-N) moments: means, central second moments of
+    Re and Im and their covariance, skewness m3/m2^1.5 and excess kurtosis
+    m4/m2^2 - 3 of Re z, E|z|^2, E|z|^4, E[z^2], min and max |z|^2, and the
+    mean, variance, skewness and excess kurtosis of log|z| over the samples
+    with |z|^2 > 0.  Counts: |z|^2 > 0, |z|^2 >= threshold, and
+    |Im z| <= real_tol |z|, where |z|^2 = re*re + im*im with each product and
+    the sum rounded to double (numpy float64, no fused multiply-add) and
+    |z| = sqrt(|z|^2).  Central moments are taken about the means (second
+    pass); every sum is math.fsum.
+    """
+    z = np.asarray(values)
+    re = np.ascontiguousarray(z.real, dtype=np.float64).reshape(-1)
+    im = (np.ascontiguousarray(z.imag, dtype=np.float64).reshape(-1) if np.iscomplexobj(z)
+          else np.zeros_like(re))
+    N = re.size
+    if N < 1:
+        raise ValueError("need at least one sample")
+    a2 = re * re + im * im                       # elementwise: two roundings, no fma
+    nz = a2 > 0.0
+    logs = 0.5 * np.log(a2[nz])
+    fs = math.fsum
+    mean_re, mean_im = fs(re) / N, fs(im) / N
+    dr, di = re - mean_re, im - mean_im
+    m2r = fs(dr * dr) / N
+    out = {
+        "count": N,
+        "count_nonzero": int(nz.sum()),
+        "count_above": int((a2 >= threshold).sum()),
+        "count_real": int((np.abs(im) <= real_tol * np.sqrt(a2)).sum()),
+        "mean_re": mean_re, "mean_im": mean_im,
+        "var_re": m2r, "var_im": fs(di * di) / N, "cov_re_im": fs(dr * di) / N,
+        "mean_abs2": fs(a2) / N, "mean_abs4": fs(a2 * a2) / N,
+        "mean_z2_re": fs(re * re - im * im) / N, "mean_z2_im": fs(2.0 * re * im) / N,
+        "min_abs2": float(a2.min()), "max_abs2": float(a2.max()),
+    }
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out["skew_re"] = float(np.float64(fs(dr ** 3) / N) / np.float64(m2r) ** 1.5)
+        out["exkurt_re"] = float(np.float64(fs(dr ** 4) / N) / np.float64(m2r) ** 2 - 3.0)
+        M = logs.size
+        if M:
+            lm = fs(logs) / M
+            dl = logs - lm
+            lv = fs(dl * dl) / M
+            out["log_mean"], out["log_var"] = lm, lv
+            out["log_skew"] = float(np.float64(fs(dl ** 3) / M) / np.float64(lv) ** 1.5)
+            out["log_exkurt"] = float(np.float64(fs(dl ** 4) / M) / np.float64(lv) ** 2 - 3.0)
+        else:
+            out.update(log_mean=math.nan, log_var=math.nan, log_skew=math.nan, log_exkurt=math.nan)
+    return out

@@ -73,6 +73,9 @@ def _load() -> ctypes.CDLL:
         "perm_tune_get": ([ctypes.c_int, i32], ctypes.c_int),
         "perm_autotune": ([ctypes.c_int, i32, i64, i32, P(i32)], ctypes.c_int),
         "permx_get_fp_arith": ([], ctypes.c_int),
+        "perm_c128_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
+        "perm_f64_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
+        "perm_sample_stats": ([ctypes.c_int, vp, i64, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         "permx_peak_probe": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                               P(ctypes.c_double)], ctypes.c_int),
     }
@@ -150,6 +153,63 @@ def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out,
     _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                           _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
     return out
+
+
+def perm_gather(U, rows, cols, out, stream=None):
+    """out[b] = perm(U[rows[b], :][:, cols[b]]) for a device matrix U (complex128 or
+    float64, 2-D, unit column stride) and host index arrays rows, cols of shape (batch, n)."""
+    import torch
+    rows, cols = _i32(rows), _i32(cols)
+    if rows.ndim != 2 or rows.shape != cols.shape:
+        raise ValueError("rows and cols must both have shape (batch, n)")
+    if U.dim() != 2 or U.shape[0] != U.shape[1] or U.stride(1) != 1:
+        raise ValueError("U must be a square 2-D tensor with unit column stride")
+    f = _lib.perm_c128_gather if U.dtype == torch.complex128 else _lib.perm_f64_gather
+    if U.dtype not in (torch.complex128, torch.float64):
+        raise TypeError("U must be complex128 or float64")
+    _check(f(U.data_ptr(), U.shape[0], U.stride(0), _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
+             rows.shape[1], rows.shape[0], out.data_ptr(), _stream(stream)))
+    return out
+
+
+class PermStats(ctypes.Structure):
+    """perm_stats_t: sample statistics of a batch of permanents."""
+    _fields_ = [(k, ctypes.c_int64) for k in ("count", "count_nonzero", "count_above", "count_real")] + \
+        [(k, ctypes.c_double) for k in ("mean_re", "mean_im", "var_re", "var_im", "cov_re_im", "skew_re",
+                                        "exkurt_re", "mean_abs2", "mean_abs4", "mean_z2_re", "mean_z2_im",
+                                        "min_abs2", "max_abs2", "log_mean", "log_var", "log_skew",
+                                        "log_exkurt")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def perm_sample_stats_async(values, out, threshold: float = float("inf"), real_tol: float = 0.0, stream=None):
+    """Enqueue perm_sample_stats on `stream`: values is a device complex128 or
+    float64 tensor, out a device uint8 tensor of at least sizeof(perm_stats_t)."""
+    import torch
+    if values.dtype == torch.complex128:
+        field = FIELD_C128
+    elif values.dtype == torch.float64:
+        field = FIELD_F64
+    else:
+        raise TypeError("values must be complex128 or float64")
+    if out.numel() * out.element_size() < ctypes.sizeof(PermStats):
+        raise ValueError("output buffer too small for perm_stats_t")
+    _check(_lib.perm_sample_stats(field, values.data_ptr(), values.numel(), threshold, real_tol,
+                                  out.data_ptr(), _stream(stream)))
+    return out
+
+
+def perm_sample_stats(values, threshold: float = float("inf"), real_tol: float = 0.0, stream=None) -> dict:
+    """Statistics of the device tensor `values` (see perm_sample_stats in permx.h), as a dict.
+    Synchronises the stream."""
+    import torch
+    out = torch.empty(ctypes.sizeof(PermStats), dtype=torch.uint8, device=values.device)
+    perm_sample_stats_async(values, out, threshold, real_tol, stream)
+    torch.cuda.synchronize(values.device)
+    raw = out.cpu().numpy().tobytes()
+    return PermStats.from_buffer_copy(raw).as_dict()
 
 
 class Plan:

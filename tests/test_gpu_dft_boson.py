@@ -1,0 +1,168 @@
+"""Submatrix permanents (perm_c128_gather / perm_f64_gather, paper §8 boson
+sampling) and the DFT measurements (paper §3.3 Table "dft", §4.3 geodesic
+I -> F_n) on the GPU.
+
+* gather: parity with the oracle on extracted submatrices (repeated modes
+  included), the same bits as perm_c128 / perm_f64 on the extracted
+  matrices, strided U, argument errors, and the closed-form second moment
+  E|perm(U_T)|^2 = n!(m-1)!/(m+n-1)! of an n x n submatrix of a Haar U(m);
+* DFT: perm(F_n) from the complex128 walk times n^{n/2} equals the exact
+  perm(S_n) from the F_p + CRT path; the percentile of |perm(F_n)| among
+  50,000 Haar samples and its ratio to the sample maximum (Table "dft");
+  geodesic permanents against the oracle and r(n) = |perm F_n| / min_t
+  |perm gamma(t)| on the 201-point grid t = k/200 (paper §4.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import dft_matrix, ensemble, geodesic_dft, rng
+from workloads.device import batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def px():
+    import paper_2602_10141_b300 as px
+    return px
+
+
+def _close(got, ref, rel=1e-10, scale=None):
+    s = max(abs(ref), scale or 0.0, 1e-300)
+    return abs(got - ref) <= rel * s
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_gather_parity_and_bits(px, cplx):
+    import torch
+    m, n, B = 40, 10, 300
+    U = ensemble("haar_u" if cplx else "haar_o", m, 1, seed=9)[0]
+    g = rng(21)
+    rows = np.stack([g.choice(m, n, replace=False) for _ in range(B)]).astype(np.int32)
+    cols = np.stack([g.choice(m, n, replace=False) for _ in range(B)]).astype(np.int32)
+    rows[::7, 1] = rows[::7, 0]                     # two photons leave through one mode
+    cols[::11, 2] = cols[::11, 3]                   # two photons enter through one mode
+    dt = torch.complex128 if cplx else torch.float64
+    dU = torch.from_numpy(U).cuda()
+    out = torch.empty(B, dtype=dt, device="cuda")
+    px.perm_gather(dU, rows, cols, out)
+    subs = np.stack([U[np.ix_(rows[b], cols[b])] for b in range(B)])
+    ref_dev = torch.empty(B, dtype=dt, device="cuda")
+    f = px.perm_c128 if cplx else px.perm_f64
+    f(torch.from_numpy(subs.reshape(-1)).cuda(), np.full(B, n, np.int32), np.arange(B, dtype=np.int64) * n * n,
+      ref_dev)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref_dev)                # same bits as the explicit extraction
+    got = out.cpu().numpy()
+    for b in range(0, B, 13):
+        ref = O.perm_dp(subs[b])
+        bound = O.perm_dp(np.abs(subs[b]))
+        assert _close(got[b], ref, 1e-12, 1e-3 * bound), (b, got[b], ref)
+
+
+def test_gather_strided_and_small(px):
+    import torch
+    M, m = 64, 33
+    big = ensemble("ginibre_c", M, 1, seed=4)[0]
+    dbig = torch.from_numpy(big).cuda()
+    U = dbig[:m, :m]                                # row stride M > m
+    rows = np.array([[32, 0, 5], [1, 1, 1], [7, 8, 9]], np.int32)
+    cols = np.array([[0, 32, 3], [2, 2, 2], [9, 8, 7]], np.int32)
+    out = torch.empty(3, dtype=torch.complex128, device="cuda")
+    px.perm_gather(U, rows, cols, out)
+    got = out.cpu().numpy()
+    for b in range(3):
+        ref = O.perm_dp(big[np.ix_(rows[b], cols[b])])
+        assert _close(got[b], ref, 1e-13), (b, got[b], ref)
+    # n = 1: the entry itself
+    one = torch.empty(2, dtype=torch.complex128, device="cuda")
+    px.perm_gather(U, np.array([[3], [32]], np.int32), np.array([[4], [0]], np.int32), one)
+    assert _close(complex(one[0].item()), complex(big[3, 4]), 1e-15)
+    assert _close(complex(one[1].item()), complex(big[32, 0]), 1e-15)
+
+
+def test_gather_errors(px):
+    import torch
+    U = torch.zeros((5, 5), dtype=torch.complex128, device="cuda")
+    out = torch.empty(4, dtype=torch.complex128, device="cuda")
+    with pytest.raises(px.PermxError, match="outside"):
+        px.perm_gather(U, np.array([[0, 5]], np.int32), np.array([[0, 1]], np.int32), out)
+    with pytest.raises(px.PermxError, match="outside"):
+        px.perm_gather(U, np.array([[0, 1]], np.int32), np.array([[-1, 1]], np.int32), out)
+    big = np.zeros((1, 33), np.int32)
+    with pytest.raises(px.PermxError):
+        px.perm_gather(U, big, big, out)
+    # empty batch: nothing to do
+    px.perm_gather(U, np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32), out)
+
+
+def test_submatrix_second_moment(px):
+    """E|perm(U_T)|^2 = n!(m-1)!/(m+n-1)! = 1/C(m+n-1, n) for distinct rows
+    and columns of a Haar U(m) (the symmetric power of the defining
+    representation is irreducible, so every matrix coefficient between unit
+    occupation states has second moment 1/dim)."""
+    import torch
+    m, n, per, units = 48, 6, 1000, 60
+    Us = batch("haar_u", m, units, seed=77)
+    g = rng(78)
+    vals = []
+    for u in range(units):
+        rows = np.stack([g.choice(m, n, replace=False) for _ in range(per)]).astype(np.int32)
+        cols = np.stack([g.choice(m, n, replace=False) for _ in range(per)]).astype(np.int32)
+        out = torch.empty(per, dtype=torch.complex128, device="cuda")
+        px.perm_gather(Us[u], rows, cols, out)
+        vals.append(out)
+    s = px.perm_sample_stats(torch.cat(vals))
+    mu = math.factorial(n) * math.factorial(m - 1) / math.factorial(m + n - 1)
+    N = per * units
+    se = math.sqrt(max(s["mean_abs4"] - s["mean_abs2"] ** 2, 0.0) / N)
+    assert abs(s["mean_abs2"] - mu) <= 6 * se, (s["mean_abs2"], mu, se)
+
+
+@pytest.mark.parametrize("n", [7, 9, 11, 13, 15, 17, 19, 23])
+def test_perm_dft_matches_exact_schur(px, n):
+    import torch
+    F = torch.from_numpy(dft_matrix(n).reshape(-1)).cuda()
+    out = torch.empty(1, dtype=torch.complex128, device="cuda")
+    px.perm_c128(F, [n], [0], out)
+    exact = px.perm_schur_crt(n)
+    v = complex(out.item()) * n ** (n / 2)
+    assert abs(v - exact) <= 1e-10 * abs(exact), (n, v, exact)
+
+
+# paper §3.3 Table "dft": n -> (percentile, |perm F_n| / max sample); None = not printed
+TABLE_DFT = [(7, 1.00, 1.6), (9, 0.34, None), (11, 1.00, 2.5), (13, 1.00, 6.9), (15, 0.14, None)]
+
+
+@pytest.mark.parametrize("n,pct,ratio", TABLE_DFT)
+def test_table_dft(px, n, pct, ratio):
+    import torch
+    count = 50_000
+    A = batch("haar_u", n, count, seed=500 + n)
+    out = torch.empty(count, dtype=torch.complex128, device="cuda")
+    px.perm_c128(A.reshape(-1), np.full(count, n, np.int32), np.arange(count, dtype=np.int64) * n * n, out)
+    pf = abs(O.perm_dp(dft_matrix(n)))
+    s = px.perm_sample_stats(out, threshold=pf * pf)
+    percentile = 1.0 - s["count_above"] / count
+    assert abs(percentile - pct) <= 0.02, (percentile, pct)
+    if ratio is not None:
+        assert abs(pf / math.sqrt(s["max_abs2"]) / ratio - 1) <= 0.25, (pf / math.sqrt(s["max_abs2"]), ratio)
+
+
+@pytest.mark.parametrize("n", [7, 9])
+def test_dft_geodesic_against_oracle(px, n):
+    import torch
+    ts = np.arange(201) / 200.0
+    mats = np.stack([geodesic_dft(n, t) for t in ts])
+    out = torch.empty(201, dtype=torch.complex128, device="cuda")
+    px.perm_c128(torch.from_numpy(mats.reshape(-1)).cuda(), np.full(201, n, np.int32),
+                 np.arange(201, dtype=np.int64) * n * n, out)
+    got = out.cpu().numpy()
+    ref = np.array([O.perm_dp(M) for M in mats])
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(np.abs(ref), 1e-3))
+    s = px.perm_sample_stats(out)
+    r_gpu = abs(got[-1]) / math.sqrt(s["min_abs2"])
+    r_ref = abs(ref[-1]) / np.min(np.abs(ref))
+    assert abs(r_gpu / r_ref - 1) <= 1e-9

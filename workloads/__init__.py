@@ -9,8 +9,10 @@ any of the computation being checked.
 """
 from .ensembles import (  # noqa: F401
     ENSEMBLES,
+    dft_matrix,
     ensemble,
     geodesic_cycle,
+    geodesic_dft,
     ginibre_c,
     ginibre_r,
     goe,

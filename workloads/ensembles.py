@@ -15,6 +15,14 @@ Every generator takes a ``numpy.random.Generator`` (PCG64 from
   permutation matrix (paper §4, §4.1): ``branch="principal"`` takes the
   eigenphases in (-pi, pi]; ``branch="circulant"`` takes 2 pi k / n,
   k = 0..n-1, which is the closed form of paper eq. (circulant).
+* DFT matrix F_n = (e^{2 pi i jk/n})_{j,k} / sqrt(n) (paper §1, §3.3) and the
+  geodesic gamma(t) = exp(t log F_n) towards it (paper §4.3).  F_n^4 = I, so
+  its eigenvalues lie in {1, i, -1, -i} and the spectral projectors are
+  P_lambda = (1/4) sum_{m<4} (F_n / lambda)^m; gamma(t) = sum_lambda
+  e^{i t theta_lambda} P_lambda with theta = 0, pi/2, -pi/2 for 1, i, -i and,
+  for -1, +pi (``branch="principal"``, phases in (-pi, pi]) or -pi
+  (``branch="minus"``).  No eigen-solver: the projectors are exact
+  polynomials in F_n.
 """
 from __future__ import annotations
 
@@ -103,6 +111,28 @@ def geodesic_cycle(n: int, t: float, branch: str = "principal") -> np.ndarray:
     j = np.arange(n)
     V = np.exp(2j * np.pi * np.outer(j, k) / n) / np.sqrt(n)     # columns v_k
     return np.ascontiguousarray((V * np.exp(1j * t * phi)[None, :]) @ V.conj().T)
+
+
+def dft_matrix(n: int) -> np.ndarray:
+    """F_n = S_n / sqrt(n), S_n = (e^{2 pi i jk/n})_{j,k=0}^{n-1}."""
+    j = np.arange(n)
+    return np.ascontiguousarray(np.exp(2j * np.pi * np.outer(j, j) / n) / np.sqrt(n))
+
+
+def geodesic_dft(n: int, t: float, branch: str = "principal") -> np.ndarray:
+    """gamma(t) = exp(t log F_n) on the geodesic from I to the DFT matrix."""
+    if branch not in ("principal", "minus"):
+        raise ValueError(branch)
+    F = dft_matrix(n)
+    eye = np.eye(n, dtype=np.complex128)
+    out = np.zeros((n, n), dtype=np.complex128)
+    theta_m1 = np.pi if branch == "principal" else -np.pi
+    for lam, th in ((1.0, 0.0), (1j, np.pi / 2), (-1.0, theta_m1), (-1j, -np.pi / 2)):
+        B = F / lam
+        B2 = B @ B
+        P = (eye + B + B2 + B2 @ B) / 4.0
+        out += np.exp(1j * t * th) * P
+    return np.ascontiguousarray(out)
 
 
 def random_residues(n: int, p: int, g: np.random.Generator) -> np.ndarray:
