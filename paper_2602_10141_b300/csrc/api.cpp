@@ -166,7 +166,7 @@ int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, 
     if (k0 > k1 || k1 > (1ull << n)) return fail(PERMX_EINVAL, "need k0 <= k1 <= 2^n");
     ModpRange R;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int rc = R.init(A, n, p, 0, s);   // plain Ryser: the range is over subsets of all n columns
+    int rc = R.init(A, n, p, 0, s, k1 - k0);   // plain Ryser: the range is over subsets of all n columns
     if (rc == PERMX_OK) rc = R.run(k0, k1, out);
     R.release();
     cudaError_t e = cudaStreamSynchronize(s);

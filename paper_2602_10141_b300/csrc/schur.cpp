@@ -24,13 +24,20 @@ namespace permx {
 // ---------------------------------------------------------------------------
 // single-matrix F_p range runner
 // ---------------------------------------------------------------------------
-int ModpRange::init(const uint32_t* A_dev, int n_, uint32_t p_, int nw_, cudaStream_t s_) {
+int ModpRange::init(const uint32_t* A_dev, int n_, uint32_t p_, int nw_, cudaStream_t s_, uint64_t window) {
     n = n_;
     p = p_;
     s = s_;
     nw = nw_;
     bits = walk_bits(n, nw);
     ell = chunk_log2_modp(bits);
+    if (window > 0) {
+        int lw = 0;
+        while (lw < 63 && (2ull << lw) <= window) ++lw;   // floor(log2(window))
+        int cap = lw - 19;
+        if (cap < 8) cap = 8;
+        if (ell > cap) ell = cap;
+    }
     ld = pad4(n);
     const size_t words = (size_t)(n + nw) * ld;
     PERMX_CUDA(ws_alloc(reinterpret_cast<void**>(&col), sizeof(uint32_t) * words + 256, s));
@@ -217,7 +224,7 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
         e = cudaMemcpyAsync(dA, hA.data(), sizeof(uint32_t) * n * n, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync"); break; }
         ModpRange R;
-        rc = R.init(dA, n, p, 1, s);
+        rc = R.init(dA, n, p, 1, s, slice);
         while (rc == PERMX_OK && st.cursor < total) {
             if (max_slices > 0 && slices >= max_slices) { rc = PERMX_EAGAIN; break; }
             const uint64_t next = st.cursor + slice < total ? st.cursor + slice : total;

@@ -23,7 +23,10 @@ struct ModpRange {
     uint32_t* col = nullptr;          // column-major copy + accumulator
     uint32_t* params = nullptr;       // {p, p^-1 mod 2^32}
     unsigned long long* acc = nullptr;
-    int init(const uint32_t* A_dev, int n, uint32_t p, int nw, cudaStream_t s);
+    // window > 0: the walks will cover windows of about `window` Gray indices;
+    // the chunk is shortened (to no less than 2^8 steps) so that a window
+    // still holds 2^19 chunks, several per resident thread.
+    int init(const uint32_t* A_dev, int n, uint32_t p, int nw, cudaStream_t s, uint64_t window = 0);
     int run(uint64_t k0, uint64_t k1, uint32_t* residue);   // synchronous
     void release();
 };

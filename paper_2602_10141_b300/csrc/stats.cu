@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kT) stats_pass1_kernel(const double* __restric
         s[7] = a2 < s[7] ? a2 : s[7];
         s[8] = a2 > s[8] ? a2 : s[8];
         if (a2 >= thr) ++c[1];
-        if (fabs(im) <= __dmul_rn(tol, __dsqrt_rn(a2))) ++c[2];
+        // tol = 0 (the common case) reduces to im == 0 for finite values; no square root
+        if (tol == 0.0 ? im == 0.0 : fabs(im) <= __dmul_rn(tol, __dsqrt_rn(a2))) ++c[2];
     }
     for (int q = 0; q < kS1; ++q) {
         const double r = block_tree(s[q], shd, q == 7 ? 1 : (q == 8 ? 2 : 0));
