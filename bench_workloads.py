@@ -59,6 +59,8 @@ def run(args):
         return serving(args)
     if args.workload == "paper_tables":
         return paper_tables(args)
+    if args.workload == "profile_stats":
+        return profile_stats(args)
     raise ValueError(args.workload)
 
 
@@ -114,6 +116,22 @@ def profile_fp(args):
             (px.perm_c128 if cplx else px.perm_f64)(A, [20] * 64, [i * 400 for i in range(64)], out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "64 x n=20 complex + 64 x n=20 real Ginibre", "arith": px.permx_get_fp_arith()}))
+    return 0
+
+
+def profile_stats(args):
+    """Small case for ncu: the sample-statistics kernels on 2^25 complex128 values (512 MiB)."""
+    import torch
+
+    import paper_2602_10141_b300 as px
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    vals = torch.randn(1 << 25, dtype=torch.complex128, device="cuda", generator=g)
+    out = torch.empty(256, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        px.perm_sample_stats_async(vals, out, threshold=1.0, real_tol=0.0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "perm_sample_stats on 2^25 complex128 values"}))
     return 0
 
 
