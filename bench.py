@@ -42,8 +42,8 @@ METRIC = "ryser_terms_per_s"
 UNIT = "terms/s"
 WORKLOAD = "schur_n33_fp_5primes"
 # dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch of this
-# command, from a one-pass ncu capture at full size (kernel unchanged since)
-WALK_DRAM_BYTES_PER_LAUNCH = 983698
+# command, from a one-pass ncu capture at full size (None until taken for the current kernel)
+WALK_DRAM_BYTES_PER_LAUNCH = None
 
 
 def _rank_env():

@@ -64,7 +64,7 @@ const char* permx_version(void);
 
 /* ------------------------------------------------------------------------
  * Batched permanents (paper §1 definition, §2.2 Gray-code evaluation; the
- * batches of §3.1, §4.1 and §5 are many independent matrices).
+ * batches of §3.1, §5.1 and §6 are many independent matrices).
  *
  * A       device, row-major matrices; matrix b starts at element offset[b]
  *         (elements, not bytes) and has n[b]*n[b] entries.
@@ -170,7 +170,7 @@ int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, 
                          uint32_t* out, void* stream);
 
 /* ------------------------------------------------------------------------
- * Planned batches and CUDA graphs (the batched call of paper §3-§5 repeated
+ * Planned batches and CUDA graphs (the batched call of paper §3-§7 repeated
  * over many inputs of one shape).  perm_plan_create fixes field, sizes,
  * offsets and (F_p) primes: it computes the chunk plan, allocates the
  * workspace from the library's pool and uploads the metadata, synchronising
@@ -192,13 +192,15 @@ int perm_plan_destroy(perm_plan* plan);
  * chunk length of a matrix is 2^ell Gray steps with ell a function of
  * (field, n) only, so results do not depend on batch composition; float
  * results do depend on ell (rounding), F_p results never.  perm_tune_set
- * pins ell for (field, n) (0 restores the built-in rule; ell <= 40 for F_p,
- * ell <= PERMX_MAX_ELL_FP for the float fields, whose exact 128-bit chunk
- * accumulator needs the headroom; EINVAL otherwise); perm_tune_get
+ * pins ell for (field, n) (0 restores the built-in rule; ell <=
+ * PERMX_MAX_ELL_MODP for F_p, whose chunk sums of terms below 2^31 are kept
+ * in 64 bits, ell <= PERMX_MAX_ELL_FP for the float fields, whose exact
+ * 128-bit chunk accumulator needs the headroom; EINVAL otherwise); perm_tune_get
  * returns the ell in force; perm_autotune times ell0-3 .. ell0+3 around the
  * built-in rule on a synthetic batch of `batch` n x n matrices (`reps`
  * timed passes each), keeps the fastest in the table and returns it. */
 #define PERMX_MAX_ELL_FP 16
+#define PERMX_MAX_ELL_MODP 30
 int perm_tune_set(int field, int32_t n, int32_t ell);
 int perm_tune_get(int field, int32_t n);
 int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* best_ell);
@@ -254,7 +256,7 @@ int perm_crt(const uint32_t* residues, const uint32_t* primes, int32_t k, int64_
 int perm_schur_prime_count(int32_t n);
 
 /* ------------------------------------------------------------------------
- * Serving: continuous batching of permanent requests (the batches of §3-§5
+ * Serving: continuous batching of permanent requests (the batches of §3-§7
  * arriving as a stream).  A server owns a CUDA stream, device slots for
  * matrices and partial sums, and a host queue.  serve_submit copies the
  * matrix and returns a ticket at once; admitted requests are advanced by
@@ -297,9 +299,9 @@ int serve_destroy(perm_server* h);
 
 /* ------------------------------------------------------------------------
  * Sample statistics of a batch of permanents, on the device (the
- * distributional measurements of paper §4 (Haar unitary: E|perm|^2,
- * circularity), §5 Table "orthogonal" (variance and excess kurtosis of
- * perm(O)), §6 (real-valuedness of Hermitian permanents), §7 Table
+ * distributional measurements of paper §3.2 (Haar unitary: E|perm|^2,
+ * circularity), §5.1 Table "orthogonal" (variance and excess kurtosis of
+ * perm(O)), §6.1 (real-valuedness of Hermitian permanents), §7.2 Table
  * "lognormal" (skewness and excess kurtosis of log|perm|) and the
  * anti-concentration probabilities Pr[|perm|^2 >= threshold]).
  *

@@ -24,8 +24,8 @@ What it computes, and where the paper defines it:
   cyclotomic polynomial ``Phi_n`` (definition of ``S_n``, paper §1).
 
 * ``sample_stats`` — the sample moments, counts and extremes the paper
-  reports over batches of permanents (§4 second moment and circularity, §5
-  Table "orthogonal", §6 real-valuedness, §7 Table "lognormal", the
+  reports over batches of permanents (§3.2 second moment and circularity, §5.1
+  Table "orthogonal", §6.1 real-valuedness, §7.2 Table "lognormal", the
   anti-concentration probabilities), from their textbook definitions with
   exactly rounded sums (``math.fsum``) in two passes.
 
@@ -441,7 +441,7 @@ def schur_modp_from_counts(n: int, p: int, g: int) -> int:
 
 
 def sample_stats(values, threshold: float = math.inf, real_tol: float = 0.0) -> dict:
-    """Sample statistics of a list of permanents (paper §4-§7).
+    """Sample statistics of a list of permanents (paper §3-§7).
 
     Plain (biased, divide-by-N) moments: means, central second moments of
     Re and Im and their covariance, skewness m3/m2^1.5 and excess kurtosis

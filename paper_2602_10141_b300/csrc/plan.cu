@@ -153,7 +153,7 @@ int perm_tune_set(int field, int32_t n, int32_t ell) {
     clear_error();
     int rc = check_field(field);
     if (rc) return rc;
-    if (n < 1 || n > PERMX_MAX_N_MODP || ell < 0 || ell > (field == PERMX_FIELD_MODP ? 40 : PERMX_MAX_ELL_FP))
+    if (n < 1 || n > PERMX_MAX_N_MODP || ell < 0 || ell > (field == PERMX_FIELD_MODP ? PERMX_MAX_ELL_MODP : PERMX_MAX_ELL_FP))
         return fail(PERMX_EINVAL, "bad n or chunk length");
     tune_set(field, n, ell);
     return PERMX_OK;

@@ -7,12 +7,17 @@
 // off.  The term prod_i r_i enters with sign (-1)^{|S_k|} = (-1)^k, so even
 // and odd k are summed separately (E, O) and the chunk contributes E - O.
 //
-// Arithmetic: residues are uint32 in [0, p), p < 2^31.  Modular add/sub use
-// one add and an unsigned min.  Products use Montgomery reduction with
-// R = 2^32 (T = a*b; m = T*p^{-1} mod R; (T - m p)/R = hi(T) - hi(m p) in
-// (-p, p)).  The product of n row sums by n-1 Montgomery steps carries
-// R^{-(n-1)}; the finalize step multiplies it back.  Partial sums are summed in
-// uint64 without reduction (L * 2^31 < 2^64).
+// Arithmetic: row sums are residues in [0, p), p < 2^31; modular add/sub use
+// one add and an unsigned min.  Products use signed Montgomery reduction with
+// R = 2^32 (the signed variant of Seiler, "Faster AVX2 optimized NTT
+// multiplication for Ring-LWE lattice cryptography", 2018): for |a|, |b| < p,
+// T = a*b (signed 64-bit), m = T * p^{-1} mod R taken as a signed 32-bit
+// value, and t = (T - m p) / R = hi(T) - hi(m p) exactly, since T and m p
+// agree in their low 32 bits.  |T - m p| < p 2^31 + 2^31 p, so |t| < p: the
+// product stays in (-p, p) with no correction step, and the next product
+// takes it as it is.  The product of n row sums by n-1 such steps carries
+// R^{-(n-1)}; the finalize step multiplies it back.  Terms are summed in
+// int64 without reduction (L * 2^31 < 2^63) and reduced once per chunk.
 #pragma once
 #include "common.cuh"
 
@@ -26,6 +31,23 @@ __device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p) 
     uint32_t d = r - a;           // wraps to > 2^31 > p when r < a
     return min(d, d + p);
 }
+#ifndef PERMX_MODP_SIGNED
+#define PERMX_MODP_SIGNED 1   // 0: unsigned Montgomery with a correction to [0, p) per product
+#endif
+
+#if PERMX_MODP_SIGNED
+typedef int32_t mont_t;       // product-tree values in (-p, p)
+typedef long long term_acc_t;
+// a * b * 2^-32 mod p for |a|, |b| < p, result in (-p, p)
+__device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, uint32_t p, uint32_t pinv) {
+    const long long T = (long long)a * b;
+    const int32_t m = (int32_t)((uint32_t)(unsigned long long)T * pinv);
+    const int32_t mh = __mulhi(m, (int32_t)p);
+    return (int32_t)(T >> 32) - mh;
+}
+#else
+typedef uint32_t mont_t;      // product-tree values in [0, p)
+typedef unsigned long long term_acc_t;
 // (-p, p) -> [0, p): a negative value wraps above p, so the unsigned min picks r + p
 __device__ __forceinline__ uint32_t mont_fix(uint32_t r, uint32_t p) { return min(r, r + p); }
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
@@ -35,16 +57,17 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p,
     uint32_t r = (uint32_t)(T >> 32) - mh;   // true value in (-p, p)
     return mont_fix(r, p);
 }
+#endif
 
 // prod_i r_i * R^{-(N-1)} by a balanced tree (depth log2 N) for ILP.  The
 // level loop has a fixed trip count so that, fully unrolled, every index is a
 // compile-time constant and v[] stays in registers.
 template <int N>
-__device__ __forceinline__ uint32_t prod_tree(const uint32_t (&r)[N], uint32_t p, uint32_t pinv) {
+__device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, uint32_t pinv) {
     static_assert(N <= 64, "tree depth");
-    uint32_t v[N];
+    mont_t v[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = r[i];
+    for (int i = 0; i < N; ++i) v[i] = (mont_t)r[i];
 #pragma unroll
     for (int lvl = 0; lvl < 6; ++lvl) {
         const int w = (N + (1 << lvl) - 1) >> lvl;   // live values at this level
@@ -56,6 +79,24 @@ __device__ __forceinline__ uint32_t prod_tree(const uint32_t (&r)[N], uint32_t p
         }
     }
     return v[0];
+}
+
+// dst_i = src_i +- (column j)_i mod p
+template <int N, bool SUB>
+__device__ __forceinline__ void column_step(uint32_t (&dst)[N], const uint32_t (&src)[N],
+                                            const uint32_t* __restrict__ cj, uint32_t p) {
+    constexpr int NP = pad4(N);
+    const uint4* c4 = reinterpret_cast<const uint4*>(cj);
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+        uint4 v = __ldg(c4 + q);
+        uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (4 * q + e < N)
+                dst[4 * q + e] = SUB ? mod_sub(src[4 * q + e], a[e], p) : mod_add(src[4 * q + e], a[e], p);
+        }
+    }
 }
 
 template <int N, bool SUB>
@@ -142,7 +183,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             for (int j = 0; j < N; ++j)
                 if ((S0 >> j) & 1) apply_column<N, false>(r, col + j * NP, p);
 
-            unsigned long long E = 0, O = 0;
+            term_acc_t E = 0, O = 0;
             uint64_t k = ks;
             if (k & 1) {                       // a window may start on an odd index
                 O += prod_tree<N>(r, p, pinv);
@@ -150,27 +191,32 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                 if (k < ke) toggle_column<N>(r, col, k, p);
             }
             // pairs (k even, k+1): the step k -> k+1 toggles column 0; both
-            // products are formed from independent copies, which doubles the
-            // instruction-level parallelism of the product trees
+            // products are formed from independent arrays, which doubles the
+            // instruction-level parallelism of the product trees.  r2 is
+            // computed from r and the next r from r2, so no array is copied.
             while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke) {
                 uint32_t r2[N];
-#pragma unroll
-                for (int i = 0; i < N; ++i) r2[i] = r[i];
-                if ((k >> 1) & 1) apply_column<N, true>(r2, col, p);
-                else apply_column<N, false>(r2, col, p);
+                if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p);
+                else column_step<N, false>(r2, r, col, p);
                 E += prod_tree<N>(r, p, pinv);
                 O += prod_tree<N>(r2, p, pinv);
                 k += 2;
-#pragma unroll
-                for (int i = 0; i < N; ++i) r[i] = r2[i];
-                if (k < ke) toggle_column<N>(r, col, k, p);
+                if (k >= ke) break;          // the chunk is done; r is not needed again
+                const int j = __ffsll((long long)k) - 1;
+                if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p);
+                else column_step<N, false>(r, r2, col + j * NP, p);
             }
             for (; k < ke; ++k) {              // remaining steps one at a time
                 if (k & 1) O += prod_tree<N>(r, p, pinv); else E += prod_tree<N>(r, p, pinv);
                 if (k + 1 < ke) toggle_column<N>(r, col, k + 1, p);
             }
+#if PERMX_MODP_SIGNED
+            long long d = (E - O) % (long long)p;       // |E - O| < 2^(ell+31) <= 2^63
+            part = (uint32_t)(d < 0 ? d + (long long)p : d);
+#else
             const uint32_t e = (uint32_t)(E % p), o = (uint32_t)(O % p);
             part = (e >= o) ? (e - o) : (e + p - o);
+#endif
         }
         // sum the group's partials mod p (all lanes of a group share m and p)
         for (int d = 1; d < G; d <<= 1) part = mod_add(part, __shfl_xor_sync(0xffffffffu, part, d), p);

@@ -1,5 +1,5 @@
 // Sample statistics of a batch of permanents (perm_sample_stats): the
-// distributional measurements of paper §4-§7 taken over the batched output
+// distributional measurements of paper §3-§7 taken over the batched output
 // without copying it to the host.
 //
 // Two passes over the values, each a fixed grid of blocks with a fixed-order

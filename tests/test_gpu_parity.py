@@ -254,7 +254,7 @@ def test_fp_identity_ones_and_hermitian(px, arith):
     assert got[0] == 1.0
     assert got[1] == math.factorial(10)
     assert run_fp(px, mats[2:])[0] == math.factorial(12)
-    # Hermitian => real permanent (paper §5, Proposition); the computed imaginary part is
+    # Hermitian => real permanent (paper §6.1, Proposition); the computed imaginary part is
     # rounding error and must stay within the float64 error bound of the walk
     H = ensemble("gue", 15, 4, seed=5)
     for A, v in zip(H, run_fp(px, list(H))):

@@ -5,11 +5,11 @@ walk + GPU statistics) against what the mathematics and the paper fix:
 
 * E|perm U|^2 = n! (n-1)! / (2n-1)! for Haar U(n) (Schur orthogonality on
   the symmetric power; the paper's n!/n^n is a different number), and the
-  exponential law of |perm U|^2 (paper §4, eq. "exp"), which together give
+  exponential law of |perm U|^2 (paper §3.2, eq. "exp"), which together give
   the paper's 18 % anti-concentration probability at n = 17 (§7);
-* circularity E[perm(U)^2] ~ 0 (§4);
-* Var and excess kurtosis of perm(O), Haar O(n) (§5, Table "orthogonal");
-* perm(H) real for Hermitian H (§6, Proposition "herm-real");
+* circularity E[perm(U)^2] ~ 0 (§3.2);
+* Var and excess kurtosis of perm(O), Haar O(n) (§5.1, Table "orthogonal");
+* perm(H) real for Hermitian H (§6.1, Proposition "herm-real");
 * skewness and excess kurtosis of log|perm| (§7, Table "lognormal");
 * Pr[|perm|^2 >= E/n^2], E = n! sigma^(2n), for the Gaussian ensembles (§7).
 
@@ -22,6 +22,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from conftest import read_golden
 from workloads import rng
 from workloads.device import batch
 
@@ -155,8 +156,9 @@ def test_haar_unitary_second_moment_and_circularity(px, n):
     assert s["count_real"] <= 0.01 * N_SAMPLES          # a generic complex permanent is not real
 
 
-# paper §5, Table "orthogonal": n, Var[perm(O)], excess kurtosis
-ORTHOGONAL = [(7, 7.89e-4, 0.607), (11, 3.88e-6, 0.418), (13, 2.60e-7, 0.212)]
+# paper §5.1, Table "orthogonal" (tests/golden/orthogonal_table.txt): n, Var[perm(O)], excess kurtosis;
+# n = 17, 19 are reported by the bench, not tested (kurtosis differences of ~0.1 are within sampling)
+ORTHOGONAL = [(int(r[0]), float(r[1]), float(r[2])) for r in read_golden("orthogonal_table.txt")][:3]
 
 
 @pytest.mark.parametrize("n,var,kurt", ORTHOGONAL)
@@ -179,9 +181,10 @@ def test_hermitian_permanents_are_real(px, name):
         assert s["count_real"] == 0
 
 
-# paper §7, Table "lognormal": (ensemble, n) -> (skew, excess kurtosis) of log|perm|
-LOGNORMAL = [("ginibre_c", 7, -0.48, 0.68), ("goe", 7, -0.58, 0.87), ("ginibre_r", 7, -0.77, 1.37),
-             ("gue", 7, -0.80, 1.56), ("ginibre_c", 13, -0.39, 0.65)]
+# paper §7.2, Table "lognormal" (tests/golden/lognormal_table.txt): (ensemble, n) -> (skew, excess
+# kurtosis) of log|perm|; the n = 7 rows of every ensemble and Ginibre-C at n = 13
+LOGNORMAL = [(r[0], int(r[1]), float(r[2]), float(r[3])) for r in read_golden("lognormal_table.txt")
+             if r[1] == "7" or (r[0] == "ginibre_c" and r[1] == "13")]
 
 
 @pytest.mark.parametrize("name,n,skew,kurt", LOGNORMAL)

@@ -1,4 +1,4 @@
-"""DFT inputs and the oracle on them (paper §3.3 Table "dft", §4.3): the
+"""DFT inputs and the oracle on them (paper §3.3 Table "dft", §4.2): the
 geodesic towards F_n is a one-parameter unitary group with the right end
 points, and the oracle's perm(F_n) times n^{n/2} is the exact integer
 perm(S_n) that the oracle's cyclotomic count reduction gives; the

@@ -147,7 +147,7 @@ def test_unitary_bound():
 
 
 def test_hermitian_is_real():
-    # paper §5, Proposition: Hermitian H => perm(H) real
+    # paper §6.1, Proposition: Hermitian H => perm(H) real
     g = rng(17)
     for n in (5, 8, 12):
         H = gue(n, g)

@@ -1,6 +1,6 @@
 """Seeded ensemble generation on the GPU for throughput runs (inputs only).
 
-The same recipes as ``ensembles.py`` (paper §3.1, §4.1, §5), drawn with a
+The same recipes as ``ensembles.py`` (paper §3.1, §5.1, §6), drawn with a
 seeded ``torch.Generator`` on the device so that batches of tens of thousands
 of matrices need no host round trip.  Every batch is reproducible from its
 seed; a subsample can be copied back and checked against the oracle.

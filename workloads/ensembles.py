@@ -7,16 +7,16 @@ Every generator takes a ``numpy.random.Generator`` (PCG64 from
   entries, with the phases of R's diagonal folded into Q (paper §3.1,
   Mezzadri's recipe).
 * Haar orthogonal: the same with real N(0,1) entries and the signs of R's
-  diagonal folded into Q (paper §4.1, "same pipeline").
+  diagonal folded into Q (paper §5.1, "same pipeline").
 * GUE (A+A^*)/2 with A complex Ginibre CN(0,1); GOE (A+A^T)/2 with A real
   Ginibre N(0,1); complex Ginibre CN(0,1) (Re, Im ~ N(0,1/2)); real
-  Ginibre N(0,1) (paper §5, list of ensembles).
+  Ginibre N(0,1) (paper §6, list of ensembles).
 * Cycle geodesic gamma(t) = Q diag(e^{i t theta_k}) Q^* towards the n-cycle
   permutation matrix (paper §4, §4.1): ``branch="principal"`` takes the
   eigenphases in (-pi, pi]; ``branch="circulant"`` takes 2 pi k / n,
   k = 0..n-1, which is the closed form of paper eq. (circulant).
 * DFT matrix F_n = (e^{2 pi i jk/n})_{j,k} / sqrt(n) (paper §1, §3.3) and the
-  geodesic gamma(t) = exp(t log F_n) towards it (paper §4.3).  F_n^4 = I, so
+  geodesic gamma(t) = exp(t log F_n) towards it (paper §4.2).  F_n^4 = I, so
   its eigenvalues lie in {1, i, -1, -i} and the spectral projectors are
   P_lambda = (1/4) sum_{m<4} (F_n / lambda)^m; gamma(t) = sum_lambda
   e^{i t theta_lambda} P_lambda with theta = 0, pi/2, -pi/2 for 1, i, -i and,
