@@ -42,8 +42,8 @@ METRIC = "ryser_terms_per_s"
 UNIT = "terms/s"
 WORKLOAD = "schur_n33_fp_5primes"
 # dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch of this
-# command, from a one-pass ncu capture at full size (None until taken for the current kernel)
-WALK_DRAM_BYTES_PER_LAUNCH = None
+# command, from a one-pass ncu capture at full size of the current kernel
+WALK_DRAM_BYTES_PER_LAUNCH = 963840
 
 
 def _rank_env():
@@ -137,7 +137,7 @@ def cpu_baseline(primes, mats, target_s: float = 12.0):
     A, p = mats[0], primes[0]
     k0 = 1 << 31
     O.ryser_modp_gray_range(A, p, k0, k0 + (1 << 12))   # start the OpenMP threads
-    span = 1 << 19
+    span = 1 << 23                       # ~1 s on 16 cores: long enough for a stable rate
     t0 = time.perf_counter()
     O.ryser_modp_gray_range(A, p, k0, k0 + span)
     dt = time.perf_counter() - t0
