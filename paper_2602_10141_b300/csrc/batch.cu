@@ -48,14 +48,14 @@ int chunk_log2(Field field, int n, int bits) {
 }
 
 int chunk_log2_fp(int bits) {
-    // About 2^10 chunks per matrix so that even one small matrix spreads over
-    // many threads (a chunk's steps run serially, so its length sets the
-    // latency of a lone small matrix); at most 2^10 steps per chunk (the
-    // float64 walk's row-sum drift grows like sqrt(L) ulps, and a chunk is the
-    // unit of work a serving step cannot split); at least 2^3 steps (or the
-    // whole walk), where the O(n^2) chunk start is still small next to the n
-    // products per step.
-    int ell = bits - 10;
+    // About 2^14 chunks per matrix (2^(bits-3) for small walks) so that even
+    // one matrix spreads over many threads (a chunk's steps run serially, so
+    // its length sets the latency of a lone matrix); at most 2^10 steps per
+    // chunk (the float64 walk's row-sum drift grows like sqrt(L) ulps, and a
+    // chunk is the unit of work a serving step cannot split); at least 2^3
+    // steps (or the whole walk), where the O(n^2) chunk start is still small
+    // next to the n products per step.
+    int ell = bits - 14;
     int lo = bits < 3 ? bits : 3;
     if (ell < lo) ell = lo;
     if (ell > 10) ell = 10;
