@@ -146,9 +146,19 @@ def cpu_baseline(primes, mats, target_s: float = 12.0):
     t0 = time.perf_counter()
     O.ryser_modp_gray_range(A, p, k0, k0 + span)
     dt = time.perf_counter() - t0
-    return {"value": N * span / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    cores = O.num_threads()
+    # the same oracle on one core, on a sample 1/cores as long (about the same seconds)
+    O.set_num_threads(1)
+    span1 = max(span // max(cores, 1), 1 << 16)
+    t1 = time.perf_counter()
+    O.ryser_modp_gray_range(A, p, k0, k0 + span1)
+    dt1 = time.perf_counter() - t1
+    O.set_num_threads(cores)
+    return {"value": N * span / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"Gray indices [{k0}, {k0 + span}) of S_33 mod {p} (one of 5 primes), "
-                      f"{span} subsets x {N} rows, {dt:.1f} s"}
+                      f"{span} subsets x {N} rows, {dt:.1f} s",
+            "single_core": {"value": N * span1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"Gray indices [{k0}, {k0 + span1}), {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):

@@ -85,6 +85,8 @@ def _load():
         lib.oracle_schur_counts.restype = i
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = i
+        lib.oracle_set_num_threads.argtypes = [i]
+        lib.oracle_set_num_threads.restype = None
         _lib = lib
     return _lib
 
@@ -117,6 +119,11 @@ class use_library:
 def num_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Use k OpenMP threads in the following calls (timing on one core or on all)."""
+    _load().oracle_set_num_threads(int(k))
 
 
 def _real(A) -> tuple[np.ndarray, int]:

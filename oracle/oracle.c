@@ -412,3 +412,5 @@ int oracle_schur_counts(int n, uint64_t* out) {
 }
 
 int oracle_num_threads(void) { return omp_get_max_threads(); }
+/* threads for the following parallel loops (k >= 1) */
+void oracle_set_num_threads(int k) { if (k >= 1) omp_set_num_threads(k); }

@@ -22,8 +22,7 @@ def test_corrupt_checkpoint_rejected(px, tmp_path):
 
 
 def test_checkpoint_from_other_run_rejected(px, tmp_path):
-    # a well-formed file (valid checksum) written for n = 17 is refused for n = 19
-    import hashlib  # noqa: F401
+    # a well-formed file (valid FNV-1a checksum) written for n = 17 is refused for n = 19
     body = "permx-schur-ckpt 2\nn 17\nprimes 2 2147483647 2147483629\ndone 0\ncursor 0 0\n"
     h = 1469598103934665603
     for c in body.encode():

@@ -5,7 +5,6 @@ ranks agree; the max-over-ranks timing reduction is exercised too."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 N_TEST = 11   # small Schur matrix so the oracle residues take milliseconds
