@@ -381,6 +381,11 @@ def serving(args):
     _, span = _drive(S, cal, [0.0] * len(cal))
     S.close()
     capacity = len(cal) / span
+    # the same sample through the plain FIFO server: its saturated throughput
+    S = _Server(px, plain=1)
+    _, span_plain = _drive(S, cal, [0.0] * len(cal))
+    S.close()
+    plain_capacity = len(cal) / span_plain
     rate = 0.7 * capacity
     g = np.random.default_rng(1)
     arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
@@ -395,7 +400,9 @@ def serving(args):
                      "throughput_rps": count / span, "makespan_s": span, "steps": st[3], "launches": st[4]}
     line = {"workload": "serving", "metric": "p99_latency_ms", "value": out["continuous"]["p99_ms"], "unit": "ms",
             "higher_is_better": False, "requests": count, "arrival_rate_rps": rate,
-            "capacity_rps": capacity, "continuous": out["continuous"], "plain_fifo": out["plain_fifo"],
+            "capacity_rps": capacity, "saturated_rps": {"continuous": capacity, "plain_fifo": plain_capacity,
+                                                        "requests": len(cal)},
+            "continuous": out["continuous"], "plain_fifo": out["plain_fifo"],
             "dtype": "c128+f64+u32", "data": "synthetic Poisson trace, seed 0",
             "config": {"mix": "1/4 each: c128 Haar n~U[10,26], f64 GOE n~U[10,26], c128 cycle geodesic odd n in "
                               "[9,25] t in k/200, F_p random n~U[16,30] with the largest p = 1 (mod n) < 2^31",
