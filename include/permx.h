@@ -84,7 +84,9 @@ const char* permx_version(void);
  * 62-bit integer mantissas on the integer pipes, summing each chunk exactly;
  * PERMX_FP_ARITH_FP64 uses IEEE float64 row sums and products with TwoSum
  * compensated accumulation.  Both use the Nijenhuis-Wilf form of Ryser's
- * formula (2^(n-1) Gray steps).
+ * formula (2^(n-1) Gray steps).  A matrix with a NaN or infinite entry gives
+ * NaN (NaN + i NaN) in integer mode, without affecting the other matrices;
+ * FP64 mode follows IEEE propagation.
  * Errors: PERMX_EINVAL for n[b] outside [1, PERMX_MAX_N_FP], NULL pointers or
  * batch < 0; PERMX_ENOMEM; PERMX_ECUDA.  On error nothing is guaranteed about
  * out.

@@ -125,11 +125,14 @@ int sm_count() {
 template <int W>
 __global__ void stage_x64_kernel(const double* __restrict__ A, const StageDesc* __restrict__ d,
                                  int64_t* __restrict__ colT) {
-    __shared__ int sig_sum;
+    __shared__ int sig_sum, bad;
     const StageDesc s = d[blockIdx.x];
     const int n = s.n, ld = s.ld;
     int64_t* base = colT + s.dst * W;   // dst counts entries of W words
-    if (threadIdx.x == 0) sig_sum = 0;
+    if (threadIdx.x == 0) {
+        sig_sum = 0;
+        bad = 0;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < ld; i += blockDim.x) {
         if (i >= n) {
@@ -140,12 +143,16 @@ __global__ void stage_x64_kernel(const double* __restrict__ A, const StageDesc* 
         const double* row = A + (s.src + (int64_t)i * n) * W;
         double S = 0.0;
         for (int j = 0; j < n * W; ++j) S += fabs(row[j]);
-        const int sig = S > 0.0 ? 60 - ilogb(S) : 0;
+        // a NaN or infinite entry makes S non-finite: the matrix is flagged (its
+        // permanent is reported as NaN) and staged as zeros
+        const bool finite = isfinite(S);
+        if (!finite) atomicOr(&bad, 1);
+        const int sig = finite && S > 0.0 ? 60 - ilogb(S) : 0;
         int64_t sum[W];
         for (int w = 0; w < W; ++w) sum[w] = 0;
         for (int j = 0; j < n; ++j)
             for (int w = 0; w < W; ++w) {
-                const int64_t a = 2 * (int64_t)llrint(ldexp(row[j * W + w], sig - 1));
+                const int64_t a = finite ? 2 * (int64_t)llrint(ldexp(row[j * W + w], sig - 1)) : 0;
                 base[((int64_t)j * ld + i) * W + w] = a;
                 sum[w] += a;
             }
@@ -156,7 +163,7 @@ __global__ void stage_x64_kernel(const double* __restrict__ A, const StageDesc* 
     __syncthreads();
     if (threadIdx.x == 0) {
         base[(int64_t)(n + 1) * ld * W] = -(int64_t)sig_sum;
-        base[(int64_t)(n + 1) * ld * W + 1] = 0;
+        base[(int64_t)(n + 1) * ld * W + 1] = bad;   // 1: non-finite entry, result NaN
     }
 }
 

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
         XAcc acc;
         x64_acc_init(acc);
         int scale = 0;
+        bool nonfinite = false;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const int64_t* col = reinterpret_cast<const int64_t*>(cold);
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
                 }
             }
             scale = (int)col[(N + 1) * NP];
+            nonfinite = col[(N + 1) * NP + 1] != 0;
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
         x64_group_merge(acc, G);
         if ((lane & (G - 1)) == 0 && valid) {
             x64_acc_to_dd(acc, scale, s, comp);
+            if (nonfinite) s = comp = __longlong_as_double(0x7ff8000000000000ll);
             reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
         }
     }
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
         x64_acc_init(ar);
         x64_acc_init(ai);
         int scale = 0;
+        bool nonfinite = false;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const longlong2* col = reinterpret_cast<const longlong2*>(cold);
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
                 }
             }
             scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
+            nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
         if ((lane & (G - 1)) == 0 && valid) {
             x64_acc_to_dd(ar, scale, sr, cr);
             x64_acc_to_dd(ai, scale, si, ci);
+            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
             double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
             out[0] = make_double2(sr, cr);
             out[1] = make_double2(si, ci);
@@ -252,6 +258,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         x64_acc_init(ar);
         x64_acc_init(ai);
         int scale = 0;
+        bool nonfinite = false;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         const unsigned pair_mask = __ballot_sync(0xffffffffu, valid);   // both lanes of a pair agree
         if (valid) {
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 }
             }
             scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
+            nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
@@ -336,6 +344,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         if ((lane & (2 * G - 1)) == 0 && valid) {
             x64_acc_to_dd(ar, scale, sr, cr);
             x64_acc_to_dd(ai, scale, si, ci);
+            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
             double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
             out[0] = make_double2(sr, cr);
             out[1] = make_double2(si, ci);

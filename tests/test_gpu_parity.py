@@ -274,6 +274,29 @@ def test_fp_alone_equals_in_mix(px, arith):
     assert mix_r[-1] == alone_r
 
 
+@pytest.mark.parametrize("cplx", [True, False])
+def test_nonfinite_entries_give_nan(px, cplx):
+    """Integer mode: a matrix with a NaN or infinite entry gives NaN and leaves
+    the other matrices of the batch bit-identical."""
+    old = px.permx_set_fp_arith(px.FP_ARITH_INT)
+    try:
+        name = "haar_u" if cplx else "goe"
+        good = [ensemble(name, n, 1, seed=60 + n)[0] for n in (7, 18, 23)]
+        bad_nan = ensemble(name, 18, 1, seed=70)[0].copy()
+        bad_nan[3, 5] = np.nan
+        bad_inf = ensemble(name, 7, 1, seed=71)[0].copy()
+        bad_inf[6, 0] = -np.inf
+        bad_big = ensemble(name, 23, 1, seed=72)[0].copy()
+        bad_big[0, 0] = np.inf if not cplx else complex(0.0, np.inf)
+        clean = run_fp(px, good)
+        mixed = run_fp(px, [good[0], bad_nan, good[1], bad_inf, bad_big, good[2]])
+        assert np.array_equal(mixed[[0, 2, 5]], clean)
+        for v in mixed[[1, 3, 4]]:
+            assert np.isnan(v.real) and (not cplx or np.isnan(v.imag))
+    finally:
+        px.permx_set_fp_arith(old)
+
+
 def test_host_variants_match_device(px, arith):
     mats = [ensemble("haar_u", n, 1, seed=3000 + n)[0] for n in (4, 11, 15)]
     flat, n, off = _pack(mats)
