@@ -27,8 +27,8 @@ namespace permx {
 // `lanes` lanes (xor butterfly of symmetric merges), in integers: the
 // double-double conversion then happens once per group instead of once per
 // chunk, which keeps the slow FP64 pipe out of the per-chunk path.
-__device__ __forceinline__ void x64_group_merge(XAcc& a, int lanes) {
-    for (int d = 1; d < lanes; d <<= 1) {
+__device__ __forceinline__ void x64_group_merge(XAcc& a, int lanes, int first = 1) {
+    for (int d = first; d < lanes; d <<= 1) {
         XAcc b;
         const uint64_t lo = (uint64_t)a.acc, hi = (uint64_t)(a.acc >> 64);
         const uint64_t blo = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo, d);
@@ -254,9 +254,8 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
-        XAcc ar, ai;
-        x64_acc_init(ar);
-        x64_acc_init(ai);
+        XAcc acc;                // even lane of a pair: Re of the terms; odd lane: Im
+        x64_acc_init(acc);
         int scale = 0;
         bool nonfinite = false;
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
@@ -331,16 +330,22 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 o.e = __shfl_xor_sync(pair_mask, p.e, 1);
                 const XCplx a = h ? o : p, b = h ? p : o;
                 const XCplx t2 = x64c_mul(a, b.re, b.im, b.e);
-                x64_acc_add(ar, t2.re, t2.e, k & 1);
-                x64_acc_add(ai, t2.im, t2.e, k & 1);
+                x64_acc_add(acc, h ? t2.im : t2.re, t2.e, k & 1);
             }
         }
-        if (h) {                 // the odd lane holds the same sums: count them once
-            x64_acc_init(ar);
-            x64_acc_init(ai);
+        // merge even lanes with even lanes (Re) and odd with odd (Im), then the
+        // group's leader takes the Im sum from its odd neighbour
+        x64_group_merge(acc, 2 * G, 2);
+        XAcc ai;
+        {
+            const uint64_t lo = (uint64_t)acc.acc, hi = (uint64_t)(acc.acc >> 64);
+            const uint64_t blo = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo, 1);
+            const uint64_t bhi = (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)hi, 1);
+            ai.acc = (__int128)(((unsigned __int128)bhi << 64) | blo);
+            ai.E = __shfl_xor_sync(0xffffffffu, acc.E, 1);
+            ai.set = __shfl_xor_sync(0xffffffffu, (int)acc.set, 1) != 0;
         }
-        x64_group_merge(ar, 2 * G);
-        x64_group_merge(ai, 2 * G);
+        const XAcc ar = acc;
         if ((lane & (2 * G - 1)) == 0 && valid) {
             x64_acc_to_dd(ar, scale, sr, cr);
             x64_acc_to_dd(ai, scale, si, ci);

@@ -25,15 +25,18 @@ __host__ __device__ __forceinline__ int x64_clz(uint64_t v) {
 #endif
 }
 
+__host__ __device__ __forceinline__ uint32_t x64_hiword(int64_t x) { return (uint32_t)((uint64_t)x >> 32); }
+
 // (a * b) >> 62 for |a|, |b| <= 2^62 (so the result fits), truncated: the
 // result is within [-2, +1] of floor(a*b / 2^62).  Balanced 32-bit limbs
 // a = a1 2^32 + a0 with a0 in [-2^31, 2^31) keep every partial product a
 // signed 32x32 -> 64 multiply; a0*b0 (< 2^62 in size) is dropped.
 __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
-    const int32_t a0 = (int32_t)(uint32_t)(uint64_t)a;
-    const int32_t b0 = (int32_t)(uint32_t)(uint64_t)b;
-    const int32_t a1 = (int32_t)((a - (int64_t)a0) >> 32);
-    const int32_t b1 = (int32_t)((b - (int64_t)b0) >> 32);
+    const uint32_t al = (uint32_t)(uint64_t)a, bl = (uint32_t)(uint64_t)b;
+    const int32_t a0 = (int32_t)al, b0 = (int32_t)bl;
+    // a = a1 2^32 + a0 with a0 = al - 2^32 when al >= 2^31: a1 = high word + that carry
+    const int32_t a1 = (int32_t)x64_hiword(a) + (int32_t)(al >> 31);
+    const int32_t b1 = (int32_t)x64_hiword(b) + (int32_t)(bl >> 31);
     const int64_t hh = (int64_t)a1 * (int64_t)b1;
     const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
     return hh * 4 + (mid >> 30);
@@ -45,7 +48,6 @@ __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
 // high word is zero (|x| < 2^32, only when a row sum is tiny) is shifted by
 // the largest such amount and stays partly normalised: its term is tiny and
 // its absolute error is still bounded by the scale of typical terms.
-__host__ __device__ __forceinline__ uint32_t x64_hiword(int64_t x) { return (uint32_t)((uint64_t)x >> 32); }
 __host__ __device__ __forceinline__ uint32_t x64_mag_hi(int64_t x) {
     const uint32_t h = x64_hiword(x);
     return h ^ (uint32_t)((int32_t)h >> 31);   // |x| >> 32 (one less for negative x)
@@ -57,11 +59,13 @@ __host__ __device__ __forceinline__ int x64_clz32(uint32_t v) {
     return v ? __builtin_clz(v) : 32;
 #endif
 }
-// Shift that puts the top bit of max |x| at position T-1 (T >= 33), in [0, 31].
+// Shift that puts the top bit of max |x| at position T-1 (33 <= T <= 63), in
+// [0, T - 32]: clz32 <= 32 bounds it from above, so only the lower clamp is needed.
 template <int T>
 __host__ __device__ __forceinline__ int x64_norm_shift_hi(uint32_t mag_hi_or) {
+    static_assert(T >= 33 && T <= 63, "shift range");
     const int s = x64_clz32(mag_hi_or) - (64 - T);
-    return s < 0 ? 0 : (s > 31 ? 31 : s);
+    return s < 0 ? 0 : s;
 }
 // x << s for 0 <= s <= 31, as two 32-bit word operations
 __host__ __device__ __forceinline__ int64_t x64_shl(int64_t x, int s) {
