@@ -59,14 +59,6 @@ __host__ __device__ __forceinline__ int x64_clz32(uint32_t v) {
     return v ? __builtin_clz(v) : 32;
 #endif
 }
-// Shift that puts the top bit of max |x| at position T-1 (33 <= T <= 63), in
-// [0, T - 32]: clz32 <= 32 bounds it from above, so only the lower clamp is needed.
-template <int T>
-__host__ __device__ __forceinline__ int x64_norm_shift_hi(uint32_t mag_hi_or) {
-    static_assert(T >= 33 && T <= 63, "shift range");
-    const int s = x64_clz32(mag_hi_or) - (64 - T);
-    return s < 0 ? 0 : s;
-}
 // x << s for 0 <= s <= 31, as two 32-bit word operations
 __host__ __device__ __forceinline__ int64_t x64_shl(int64_t x, int s) {
     const uint32_t lo = (uint32_t)(uint64_t)x, hi = x64_hiword(x);
@@ -82,19 +74,41 @@ struct XReal { int64_t m; int e; };
 struct XCplx { int64_t re, im; int e; };
 
 // real: mantissa target |m| in [2^61, 2^62]
+// Position of the most significant non-sign bit of the high word (-1 when the
+// word is 0 or -1): bfind.s32 on the GPU, the same value from the folded
+// magnitude on the host.
+__host__ __device__ __forceinline__ int x64_top_hi(int64_t x) {
+#ifdef __CUDA_ARCH__
+    int r;
+    asm("bfind.s32 %0, %1;" : "=r"(r) : "r"((int32_t)x64_hiword(x)));
+    return r;
+#else
+    return 31 - x64_clz32(x64_mag_hi(x));
+#endif
+}
+// Shift that puts the top non-sign bit (position `top` of the high word) at
+// bit T-1 of the 64-bit value: T - 33 - top, at least 0 and at most T - 32
+// (top >= -1), so 33 <= T <= 63 keeps it within a funnel shift.
+template <int T>
+__host__ __device__ __forceinline__ int x64_norm_shift_top(int top) {
+    const int s = T - 33 - top;
+    return s < 0 ? 0 : s;
+}
+
 __host__ __device__ __forceinline__ XReal x64_from_int(int64_t r) {
-    const int s = x64_norm_shift_hi<62>(x64_mag_hi(r));
+    const int s = x64_norm_shift_top<62>(x64_top_hi(r));
     return XReal{x64_shl(r, s), -s};
 }
 __host__ __device__ __forceinline__ XReal x64_mul(XReal a, int64_t m2, int e2) {
     const int64_t x = x64_mulhi62(a.m, m2);
-    const int s = x64_norm_shift_hi<62>(x64_mag_hi(x));
+    const int s = x64_norm_shift_top<62>(x64_top_hi(x));
     return XReal{x64_shl(x, s), a.e + e2 + 62 - s};
 }
 
 // complex: larger component target in [2^60, 2^61] (sums of two stay below 2^62)
 __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) {
-    const int s = x64_norm_shift_hi<61>(x64_mag_hi(re) | x64_mag_hi(im));
+    const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
+    const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), -s};
 }
 // (a.re + i a.im) * (br + i bi) * 2^-62, |br|, |bi| <= 2^61; three products
@@ -106,7 +120,8 @@ __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t 
     const int64_t k2 = x64_mulhi62(a.re, bi - br);
     const int64_t k3 = x64_mulhi62(a.im, br + bi);
     const int64_t re = k1 - k3, im = k1 + k2;
-    const int s = x64_norm_shift_hi<61>(x64_mag_hi(re) | x64_mag_hi(im));
+    const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
+    const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
 }
 
