@@ -593,7 +593,7 @@ def paper_tables(args):
           "hbm_gbs": 2 * 16 * big / ms / 1e6, "hbm_peak_gbs": hbm,
           "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "FP64 instr/s",
                        "frac": achieved / peak, "fp64_inst_per_value": fp64_per_value,
-                       "source": "FP64-pipe instruction count per value from ncu (profiles/sample_stats_c128.md)"}})
+                       "source": "FP64-pipe instructions per value from an ncu capture of --workload profile_stats"}})
     emit({"workload": "paper_tables", "wall_s": time.perf_counter() - t_start, "walk_ms": walk_ms,
           "walk_nominal_terms_per_s": walk_terms / walk_ms * 1e3})
     return 0

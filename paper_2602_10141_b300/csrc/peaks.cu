@@ -1,5 +1,5 @@
 // Issue-rate probes for the pipes the Ryser kernels use.  They give the
-// roofline denominators that the measured HBM / bf16 peaks do not
+// roofline denominators that the measured HBM copy and bf16 GEMM peaks do not
 // cover: FP64 (f64 / complex128 walks) and 32-bit integer (F_p walk).
 //
 // Each thread runs 8 independent dependency chains of one operation for

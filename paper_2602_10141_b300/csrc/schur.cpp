@@ -171,7 +171,7 @@ int read_checkpoint(const std::string& path, SchurState& st) {
 }
 
 // ---------------------------------------------------------------------------
-// driver
+// the run: primes, checkpointed slices, CRT
 // ---------------------------------------------------------------------------
 int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subsets, int64_t max_slices,
                   SchurResult& res) {

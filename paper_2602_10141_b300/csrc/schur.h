@@ -1,4 +1,4 @@
-// Schur-permanent driver structures (schur.cpp) and the single-matrix F_p
+// Schur-permanent run structures (schur.cpp) and the single-matrix F_p
 // range runner shared with the serving loop.
 #pragma once
 #include <cuda_runtime.h>
