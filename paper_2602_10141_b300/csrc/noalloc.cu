@@ -69,6 +69,19 @@ __global__ void noalloc_setup_kernel(const uint32_t* __restrict__ A, const Noall
         const int j = e / ld, i = e % ld;
         colT[e] = i < n ? A[args.src[k] + (int64_t)i * n + j] : 0u;
     }
+    // Nijenhuis-Wilf column x_i = a_{i,n-1} - (1/2) sum_j a_ij mod p, with 1/2 = (p+1)/2
+    const uint64_t p = args.p[k];
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+        uint32_t x = 0;
+        if (i < n) {
+            const uint32_t* row = A + args.src[k] + (int64_t)i * n;
+            uint64_t sum = 0;
+            for (int j = 0; j < n; ++j) sum += row[j];
+            const uint64_t half = (sum % p) * ((p + 1) / 2) % p;
+            x = (uint32_t)(((uint64_t)row[n - 1] + p - half) % p);
+        }
+        colT[(int64_t)n * ld + i] = x;
+    }
 }
 
 __global__ void noalloc_finalize_kernel(const NoallocArgs args, const unsigned char* __restrict__ scratch,
@@ -77,8 +90,9 @@ __global__ void noalloc_finalize_kernel(const NoallocArgs args, const unsigned c
     if (k >= args.count) return;
     const uint64_t p = args.p[k];
     const unsigned long long acc = reinterpret_cast<const unsigned long long*>(scratch + kOffAcc)[k];
+    // rfix = 2 R^(n-1) mod p; perm = (-1)^(n-1) 2 sum
     uint32_t v = (uint32_t)((acc % p) * (uint64_t)args.rfix[k] % p);
-    if ((args.n[k] & 1) && v) v = (uint32_t)p - v;
+    if (!(args.n[k] & 1) && v) v = (uint32_t)p - v;
     out[args.out_index[k]] = v;
 }
 
@@ -142,9 +156,10 @@ extern "C" int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int6
         args.col[k] = (int64_t)words;
         args.p[k] = p[b];
         args.pinv[k] = inv_mod_2_32(p[b]);
-        args.rfix[k] = pow_mod((uint32_t)((1ull << 32) % p[b]), (uint64_t)(n[b] - 1), p[b]);
+        args.rfix[k] = (uint32_t)((uint64_t)pow_mod((uint32_t)((1ull << 32) % p[b]), (uint64_t)(n[b] - 1), p[b]) *
+                                  2 % p[b]);
         args.out_index[k] = b;
-        words += (size_t)n[b] * pad4(n[b]);
+        words += (size_t)(n[b] + 1) * pad4(n[b]);   // n columns and the x column
     }
     if (kOffCol + 4 * words > (size_t)PERMX_NOALLOC_SCRATCH_BYTES)
         return fail(PERMX_EINVAL, "perm_modp_noalloc: matrices exceed PERMX_NOALLOC_SCRATCH_BYTES");
@@ -165,13 +180,15 @@ extern "C" int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int6
         L.p = reinterpret_cast<const uint32_t*>(scratch + kOffP) + k0;
         L.pinv = reinterpret_cast<const uint32_t*>(scratch + kOffPinv) + k0;
         L.acc = reinterpret_cast<unsigned long long*>(scratch + kOffAcc) + k0;
-        L.mat_stride = (int64_t)nn * pad4(nn);
-        L.ell = chunk_log2_modp(nn);   // plain Ryser form: the walk covers all nn columns
-        L.log2_chunks = nn - L.ell;
+        L.mat_stride = (int64_t)(nn + 1) * pad4(nn);
+        const int bits = walk_bits(nn, 1);   // Nijenhuis-Wilf form: 2^(nn-1) Gray steps
+        L.ell = chunk_log2_modp(bits);
+        L.log2_chunks = bits - L.ell;
         L.item_begin = 0;
         L.item_end = (uint64_t)(k1 - k0) << L.log2_chunks;
         L.k_lo = 0;
-        L.k_hi = 1ull << nn;
+        L.k_hi = 1ull << bits;
+        L.nw = 1;
         PERMX_CUDA(dispatch_modp(nn, L, s));
         k0 = k1;
     }
