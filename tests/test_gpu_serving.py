@@ -200,3 +200,31 @@ def test_memory_bound_admission_and_limits(px):
         assert rc == px.PERMX_EINVAL   # entries must be below p
     finally:
         S.close()
+
+
+def test_nonfinite_request_gives_nan_and_leaves_others(px):
+    """A served matrix with a NaN or infinite entry yields NaN (integer mode),
+    and the requests served beside it keep their batched-path bits."""
+    old = px.permx_set_fp_arith(px.FP_ARITH_INT)
+    S = Server(px)
+    try:
+        good = [(ensemble("haar_u", 12, 1, seed=900)[0], 0), (ensemble("goe", 14, 1, seed=901)[0], 1)]
+        bad_c = ensemble("haar_u", 13, 1, seed=902)[0].copy()
+        bad_c[2, 3] = complex(np.nan, 0.0)
+        bad_r = ensemble("goe", 11, 1, seed=903)[0].copy()
+        bad_r[0, 0] = np.inf
+        reqs = [good[0], (bad_c, 0), good[1], (bad_r, 1)]
+        tickets = []
+        for A, f in reqs:
+            rc, t = S.submit(A, f)
+            assert rc == 0, px.last_error()
+            tickets.append((t, f))
+        res = S.wait(tickets)
+        vals = [res[t][0] for t, _ in tickets]
+        assert vals[0] == _batched(px, good[0][0], 0)
+        assert vals[2] == _batched(px, good[1][0], 1)
+        assert np.isnan(vals[1].real) and np.isnan(vals[1].imag)
+        assert np.isnan(vals[3])
+    finally:
+        S.close()
+        px.permx_set_fp_arith(old)
