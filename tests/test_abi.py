@@ -92,3 +92,28 @@ def test_invalid_helper_arguments(px):
         px.perm_crt([1, 2], [7, 7])
     with pytest.raises(px.PermxError):
         px.perm_schur_residues(0, 7, 2)
+
+
+def test_chunk_tuning_table_host_logic(px):
+    """perm_tune_* is host logic: set / get / restore, and the limits (the F_p
+    chunk sums need ell <= 30, the float 128-bit chunk accumulator ell <= 16)."""
+    try:
+        default = px.perm_tune_get(px.FIELD_C128, 20)
+        assert 3 <= default <= 10
+        px.perm_tune_set(px.FIELD_C128, 20, 7)
+        assert px.perm_tune_get(px.FIELD_C128, 20) == 7
+        px.perm_tune_set(px.FIELD_C128, 20, 16)
+        with pytest.raises(px.PermxError):
+            px.perm_tune_set(px.FIELD_C128, 20, 17)
+        px.perm_tune_set(px.FIELD_MODP, 40, 30)
+        assert px.perm_tune_get(px.FIELD_MODP, 40) == 30
+        with pytest.raises(px.PermxError):
+            px.perm_tune_set(px.FIELD_MODP, 40, 31)
+        with pytest.raises(px.PermxError):
+            px.perm_tune_set(px.FIELD_F64, 49, 5)     # n above the table
+        with pytest.raises(px.PermxError):
+            px.perm_tune_set(7, 10, 3)                # unknown field
+    finally:
+        px.perm_tune_set(px.FIELD_C128, 20, 0)
+        px.perm_tune_set(px.FIELD_MODP, 40, 0)
+    assert px.perm_tune_get(px.FIELD_C128, 20) == default

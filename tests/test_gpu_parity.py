@@ -378,3 +378,15 @@ def test_n1_all_fields(px, arith):
     assert run_fp(px, [np.array([[2.5 - 1j]])])[0] == 2.5 - 1j
     assert run_fp(px, [np.array([[-3.25]])])[0] == -3.25
     assert int(run_modp(px, [np.array([[12345]], np.uint32)], [2147483629])[0]) == 12345
+
+
+def test_schur_crt_matches_oracle_fixture(px):
+    """Exact perm(S_n), n = 21..27, through the GPU F_p walk and the library's
+    CRT, equals the oracle's value (tests/golden/schur_crt_oracle.txt, written
+    by make_schur_crt.py from the oracle alone)."""
+    from conftest import read_golden
+    rows = read_golden("schur_crt_oracle.txt")
+    assert [int(r[0]) for r in rows] == list(range(21, 28))
+    for r in rows:
+        n, value = int(r[0]), int(r[1])
+        assert px.perm_schur_crt(n) == value, n

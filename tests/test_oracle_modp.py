@@ -169,3 +169,19 @@ def test_crt_recovers_schur_with_disjoint_prime_sets():
             assert O.crt_modulus_suffices(n, ps)
             res = [O.perm_modp(O.schur_residue_matrix(n, p, O.primitive_nth_root(p, n)), p) for p in ps]
             assert O.crt(res, ps) == x
+
+
+def test_schur_crt_fixture_consistent():
+    """The stored oracle values of perm(S_n) (n = 21..27) agree with the oracle's
+    F_p Ryser modulo a prime that the generator did not use (n = 21, 22, 23)
+    and respect |perm(S_n)|^2 <= n^n."""
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "schur_crt_oracle.txt")
+    rows = [ln.split() for ln in open(here) if ln.strip() and not ln.startswith("#")]
+    for r in rows:
+        n, value, used = int(r[0]), int(r[1]), [int(x) for x in r[2:]]
+        assert value * value <= n ** n
+        if n <= 23:
+            q = O.primes_1_mod_n(n, 1, below=min(used))[0]     # the next prime down, unused
+            S = O.schur_residue_matrix(n, q, O.primitive_nth_root(q, n))
+            assert value % q == O.perm_modp(S, q), n
