@@ -59,7 +59,8 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p,
 }
 #endif
 
-// prod_i r_i * R^{-(N-1)} by a balanced tree (depth log2 N) for ILP.  The
+// prod_i r_i * R^{-(N-1)} by a balanced tree (depth log2 N) for ILP (four
+// interleaved chains measured 1 % slower at n = 33).  The
 // level loop has a fixed trip count so that, fully unrolled, every index is a
 // compile-time constant and v[] stays in registers.
 template <int N>
