@@ -228,3 +228,21 @@ def test_nonfinite_request_gives_nan_and_leaves_others(px):
     finally:
         S.close()
         px.permx_set_fp_arith(old)
+
+
+def test_drain_reports_timeout_then_completes(px):
+    """serve_drain returns PERMX_ETIMEOUT while a long request is in flight and
+    0 once everything has finished; the result is still the batched one."""
+    S = Server(px)
+    try:
+        n = 29
+        p = O.primes_1_mod_n(n, 1)[0]
+        A = random_residues(n, p, rng(77))            # 2^28 Gray steps: milliseconds on the GPU
+        rc, t = S.submit(A, 2, p)
+        assert rc == 0, px.last_error()
+        assert S.lib.serve_drain(S.h, 0) == px.PERMX_ETIMEOUT
+        assert S.lib.serve_drain(S.h, 60_000) == 0, px.last_error()
+        res = S.wait([(t, 2)])
+        assert res[t][0] == _batched(px, A, 2, p)
+    finally:
+        S.close()
