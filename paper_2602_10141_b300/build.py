@@ -60,7 +60,7 @@ def _gen_dispatch() -> None:
                 "    };",
                 "    switch (n) {"]
         for n in range(1, mx + 1):
-            lanes = 2 if (kind == "x64c" and n > 16) else 1   # x64c_paired(n)
+            lanes = f"x64c_paired({n}) ? 2 : 1" if kind == "x64c" else "1"
             out.append(f"        case {n}: return launch_{kind}<{n}>(L, grid_for(blocks_per_sm_{kind}<{n}>(), {lanes}), s);")
         out += ["        default: return cudaErrorInvalidValue;", "    }", "}", ""]
     # resident blocks per SM of the kernel that a (kind, n) launch uses

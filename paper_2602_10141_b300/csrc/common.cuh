@@ -123,7 +123,13 @@ int dispatch_blocks_per_sm(int kind, int n);
 // Complex integer-mantissa walks with n > 16 run two lanes per chunk, so a
 // warp covers 16 chunks instead of 32; chunk lane groups (and the partial
 // slots per matrix) follow from this.
-constexpr bool x64c_paired(int n) { return n > 16; }
+#ifndef PERMX_X64C_PAIR_MIN_N
+#define PERMX_X64C_PAIR_MIN_N 17   // complex integer-mantissa walks with n >= this use two lanes per chunk
+#endif
+// (pairing from n = 10 measured 15 % faster for one lone matrix at n = 14-16 but
+// 20 % slower for batches of thousands, which is what the threshold serves)
+static_assert(PERMX_X64C_PAIR_MIN_N >= 8, "each lane of a pair needs at least four rows");
+constexpr bool x64c_paired(int n) { return n >= PERMX_X64C_PAIR_MIN_N; }
 inline int chunks_per_warp(bool x64, bool cplx, int n) { return (x64 && cplx && x64c_paired(n)) ? 16 : 32; }
 inline int group_log2(int log2_chunks, int per_warp) {
     const int w = per_warp == 16 ? 4 : 5;

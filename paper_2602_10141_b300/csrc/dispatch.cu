@@ -208,38 +208,38 @@ cudaError_t dispatch_x64c(int n, const FpLaunch& L, cudaStream_t s) {
         return (int)(want < cap ? want : cap);
     };
     switch (n) {
-        case 1: return launch_x64c<1>(L, grid_for(blocks_per_sm_x64c<1>(), 1), s);
-        case 2: return launch_x64c<2>(L, grid_for(blocks_per_sm_x64c<2>(), 1), s);
-        case 3: return launch_x64c<3>(L, grid_for(blocks_per_sm_x64c<3>(), 1), s);
-        case 4: return launch_x64c<4>(L, grid_for(blocks_per_sm_x64c<4>(), 1), s);
-        case 5: return launch_x64c<5>(L, grid_for(blocks_per_sm_x64c<5>(), 1), s);
-        case 6: return launch_x64c<6>(L, grid_for(blocks_per_sm_x64c<6>(), 1), s);
-        case 7: return launch_x64c<7>(L, grid_for(blocks_per_sm_x64c<7>(), 1), s);
-        case 8: return launch_x64c<8>(L, grid_for(blocks_per_sm_x64c<8>(), 1), s);
-        case 9: return launch_x64c<9>(L, grid_for(blocks_per_sm_x64c<9>(), 1), s);
-        case 10: return launch_x64c<10>(L, grid_for(blocks_per_sm_x64c<10>(), 1), s);
-        case 11: return launch_x64c<11>(L, grid_for(blocks_per_sm_x64c<11>(), 1), s);
-        case 12: return launch_x64c<12>(L, grid_for(blocks_per_sm_x64c<12>(), 1), s);
-        case 13: return launch_x64c<13>(L, grid_for(blocks_per_sm_x64c<13>(), 1), s);
-        case 14: return launch_x64c<14>(L, grid_for(blocks_per_sm_x64c<14>(), 1), s);
-        case 15: return launch_x64c<15>(L, grid_for(blocks_per_sm_x64c<15>(), 1), s);
-        case 16: return launch_x64c<16>(L, grid_for(blocks_per_sm_x64c<16>(), 1), s);
-        case 17: return launch_x64c<17>(L, grid_for(blocks_per_sm_x64c<17>(), 2), s);
-        case 18: return launch_x64c<18>(L, grid_for(blocks_per_sm_x64c<18>(), 2), s);
-        case 19: return launch_x64c<19>(L, grid_for(blocks_per_sm_x64c<19>(), 2), s);
-        case 20: return launch_x64c<20>(L, grid_for(blocks_per_sm_x64c<20>(), 2), s);
-        case 21: return launch_x64c<21>(L, grid_for(blocks_per_sm_x64c<21>(), 2), s);
-        case 22: return launch_x64c<22>(L, grid_for(blocks_per_sm_x64c<22>(), 2), s);
-        case 23: return launch_x64c<23>(L, grid_for(blocks_per_sm_x64c<23>(), 2), s);
-        case 24: return launch_x64c<24>(L, grid_for(blocks_per_sm_x64c<24>(), 2), s);
-        case 25: return launch_x64c<25>(L, grid_for(blocks_per_sm_x64c<25>(), 2), s);
-        case 26: return launch_x64c<26>(L, grid_for(blocks_per_sm_x64c<26>(), 2), s);
-        case 27: return launch_x64c<27>(L, grid_for(blocks_per_sm_x64c<27>(), 2), s);
-        case 28: return launch_x64c<28>(L, grid_for(blocks_per_sm_x64c<28>(), 2), s);
-        case 29: return launch_x64c<29>(L, grid_for(blocks_per_sm_x64c<29>(), 2), s);
-        case 30: return launch_x64c<30>(L, grid_for(blocks_per_sm_x64c<30>(), 2), s);
-        case 31: return launch_x64c<31>(L, grid_for(blocks_per_sm_x64c<31>(), 2), s);
-        case 32: return launch_x64c<32>(L, grid_for(blocks_per_sm_x64c<32>(), 2), s);
+        case 1: return launch_x64c<1>(L, grid_for(blocks_per_sm_x64c<1>(), x64c_paired(1) ? 2 : 1), s);
+        case 2: return launch_x64c<2>(L, grid_for(blocks_per_sm_x64c<2>(), x64c_paired(2) ? 2 : 1), s);
+        case 3: return launch_x64c<3>(L, grid_for(blocks_per_sm_x64c<3>(), x64c_paired(3) ? 2 : 1), s);
+        case 4: return launch_x64c<4>(L, grid_for(blocks_per_sm_x64c<4>(), x64c_paired(4) ? 2 : 1), s);
+        case 5: return launch_x64c<5>(L, grid_for(blocks_per_sm_x64c<5>(), x64c_paired(5) ? 2 : 1), s);
+        case 6: return launch_x64c<6>(L, grid_for(blocks_per_sm_x64c<6>(), x64c_paired(6) ? 2 : 1), s);
+        case 7: return launch_x64c<7>(L, grid_for(blocks_per_sm_x64c<7>(), x64c_paired(7) ? 2 : 1), s);
+        case 8: return launch_x64c<8>(L, grid_for(blocks_per_sm_x64c<8>(), x64c_paired(8) ? 2 : 1), s);
+        case 9: return launch_x64c<9>(L, grid_for(blocks_per_sm_x64c<9>(), x64c_paired(9) ? 2 : 1), s);
+        case 10: return launch_x64c<10>(L, grid_for(blocks_per_sm_x64c<10>(), x64c_paired(10) ? 2 : 1), s);
+        case 11: return launch_x64c<11>(L, grid_for(blocks_per_sm_x64c<11>(), x64c_paired(11) ? 2 : 1), s);
+        case 12: return launch_x64c<12>(L, grid_for(blocks_per_sm_x64c<12>(), x64c_paired(12) ? 2 : 1), s);
+        case 13: return launch_x64c<13>(L, grid_for(blocks_per_sm_x64c<13>(), x64c_paired(13) ? 2 : 1), s);
+        case 14: return launch_x64c<14>(L, grid_for(blocks_per_sm_x64c<14>(), x64c_paired(14) ? 2 : 1), s);
+        case 15: return launch_x64c<15>(L, grid_for(blocks_per_sm_x64c<15>(), x64c_paired(15) ? 2 : 1), s);
+        case 16: return launch_x64c<16>(L, grid_for(blocks_per_sm_x64c<16>(), x64c_paired(16) ? 2 : 1), s);
+        case 17: return launch_x64c<17>(L, grid_for(blocks_per_sm_x64c<17>(), x64c_paired(17) ? 2 : 1), s);
+        case 18: return launch_x64c<18>(L, grid_for(blocks_per_sm_x64c<18>(), x64c_paired(18) ? 2 : 1), s);
+        case 19: return launch_x64c<19>(L, grid_for(blocks_per_sm_x64c<19>(), x64c_paired(19) ? 2 : 1), s);
+        case 20: return launch_x64c<20>(L, grid_for(blocks_per_sm_x64c<20>(), x64c_paired(20) ? 2 : 1), s);
+        case 21: return launch_x64c<21>(L, grid_for(blocks_per_sm_x64c<21>(), x64c_paired(21) ? 2 : 1), s);
+        case 22: return launch_x64c<22>(L, grid_for(blocks_per_sm_x64c<22>(), x64c_paired(22) ? 2 : 1), s);
+        case 23: return launch_x64c<23>(L, grid_for(blocks_per_sm_x64c<23>(), x64c_paired(23) ? 2 : 1), s);
+        case 24: return launch_x64c<24>(L, grid_for(blocks_per_sm_x64c<24>(), x64c_paired(24) ? 2 : 1), s);
+        case 25: return launch_x64c<25>(L, grid_for(blocks_per_sm_x64c<25>(), x64c_paired(25) ? 2 : 1), s);
+        case 26: return launch_x64c<26>(L, grid_for(blocks_per_sm_x64c<26>(), x64c_paired(26) ? 2 : 1), s);
+        case 27: return launch_x64c<27>(L, grid_for(blocks_per_sm_x64c<27>(), x64c_paired(27) ? 2 : 1), s);
+        case 28: return launch_x64c<28>(L, grid_for(blocks_per_sm_x64c<28>(), x64c_paired(28) ? 2 : 1), s);
+        case 29: return launch_x64c<29>(L, grid_for(blocks_per_sm_x64c<29>(), x64c_paired(29) ? 2 : 1), s);
+        case 30: return launch_x64c<30>(L, grid_for(blocks_per_sm_x64c<30>(), x64c_paired(30) ? 2 : 1), s);
+        case 31: return launch_x64c<31>(L, grid_for(blocks_per_sm_x64c<31>(), x64c_paired(31) ? 2 : 1), s);
+        case 32: return launch_x64c<32>(L, grid_for(blocks_per_sm_x64c<32>(), x64c_paired(32) ? 2 : 1), s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                         }
                     }
                 }
-                // the lane's half product (rows >= 8 here, so all four chains start)
+                // the lane's half product (rows >= 4 for n >= 8, so all four chains start)
                 XCplx t[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
