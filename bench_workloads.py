@@ -61,6 +61,8 @@ def run(args):
         return paper_tables(args)
     if args.workload == "profile_stats":
         return profile_stats(args)
+    if args.workload == "batch_scaling":
+        return batch_scaling(args)
     raise ValueError(args.workload)
 
 
@@ -116,6 +118,53 @@ def profile_fp(args):
             (px.perm_c128 if cplx else px.perm_f64)(A, [20] * 64, [i * 400 for i in range(64)], out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "64 x n=20 complex + 64 x n=20 real Ginibre", "arith": px.permx_get_fp_arith()}))
+    return 0
+
+
+def batch_scaling(args):
+    """Permanents per second against batch size (one batched call of B equal-size
+    matrices, inputs resident on the device): complex128 Haar U(n) and F_p
+    random residues at n = 14 and 20, B = 1 .. 16384 (n = 14) or 4096 (n = 20)."""
+    import torch
+
+    import paper_2602_10141_b300 as px
+    from workloads.device import batch
+    rows = []
+    for field, n, sizes in (("c128", 14, (1, 4, 16, 64, 256, 1024, 4096, 16384)),
+                            ("c128", 20, (1, 4, 16, 64, 256, 1024, 4096)),
+                            ("modp", 20, (1, 4, 16, 64, 256, 1024, 4096))):
+        top = sizes[-1]
+        if field == "c128":
+            A = batch("haar_u", n, top, seed=n).reshape(-1)
+        else:                                   # residues below p = 2^31 - 1 (prime)
+            g = torch.Generator(device="cuda")
+            g.manual_seed(n)
+            A = torch.randint(0, 2 ** 31 - 1, (top * n * n,), generator=g, device="cuda", dtype=torch.int64)
+            A = A.to(torch.int32)
+        for B in sizes:
+            nn = np.full(B, n, np.int32)
+            off = np.arange(B, dtype=np.int64) * n * n
+            if field == "c128":
+                out = torch.empty(B, dtype=torch.complex128, device="cuda")
+                fn = lambda: px.perm_c128(A, nn, off, out)   # noqa: E731
+            else:
+                out = torch.empty(B, dtype=torch.int32, device="cuda")
+                pp = np.full(B, 2147483647, np.uint32)
+                fn = lambda: px.perm_modp(A, nn, off, pp, out)   # noqa: E731
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            reps = max(3, min(200, int(20000 // (B * (1 if n == 14 else 40)))))
+            e0, e1 = _events(torch)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"field": field, "n": n, "batch": B, "ms_per_call": ms, "perms_per_s": B / ms * 1e3,
+                         "evaluated_terms_per_s": B * n * 2.0 ** (n - 1) / ms * 1e3})
+    print(json.dumps({"workload": "batch_scaling", "rows": rows}), flush=True)
     return 0
 
 

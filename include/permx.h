@@ -109,7 +109,9 @@ int permx_get_fp_arith(void);
  * give unspecified results; the checked host path perm_modp_host rejects
  * them), p host array [batch] of primes 2 < p < 2^31, out device array
  * [batch] of canonical residues in [0, p[b]).  1 <= n[b] <= PERMX_MAX_N_MODP.
- * Exact: the result does not depend on chunking or batch composition. */
+ * Exact: the result does not depend on chunking or batch composition, so a
+ * call whose matrices would make fewer than 2^18 chunks shortens its chunks
+ * (down to 2^5 Gray steps) to fill the GPU, unless perm_tune_set pinned them. */
 int perm_modp(const uint32_t* A, const int32_t* n, const int64_t* offset, const uint32_t* p,
               int64_t batch, uint32_t* out, void* stream);
 
@@ -191,9 +193,10 @@ int perm_plan_graph_launch(perm_plan* plan, const void* A, void* out, void* stre
 int perm_plan_destroy(perm_plan* plan);
 
 /* Chunk-length tuning (paper §2.2: the size of a Gray-code block).  The
- * chunk length of a matrix is 2^ell Gray steps with ell a function of
- * (field, n) only, so results do not depend on batch composition; float
- * results do depend on ell (rounding), F_p results never.  perm_tune_set
+ * chunk length of a float matrix is 2^ell Gray steps with ell a function of
+ * (field, n) only, so float results do not depend on batch composition; they
+ * do depend on ell (rounding).  F_p results never depend on ell, and small
+ * F_p batches shorten their chunks (see perm_modp).  perm_tune_set
  * pins ell for (field, n) (0 restores the built-in rule; ell <=
  * PERMX_MAX_ELL_MODP for F_p, whose chunk sums of terms below 2^31 are kept
  * in 64 bits, ell <= PERMX_MAX_ELL_FP for the float fields, whose exact

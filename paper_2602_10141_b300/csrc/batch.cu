@@ -404,6 +404,34 @@ BatchPlan plan_batch(const int32_t* n, int64_t batch, Field field) {
         part_off += g.partials_per_mat * (int64_t)g.mats.size();
         P.groups.push_back(std::move(g));
     }
+    if (field == Field::MODP) {
+        // F_p results are exact whatever the chunking, so a batch too small to
+        // fill the GPU gets shorter chunks (down to 2^5 steps, or the whole walk)
+        // until the launch holds about 2^18 chunks; pinned lengths are kept.
+        const int64_t kTargetItems = (int64_t)1 << 18;
+        bool changed = true;
+        while (changed) {
+            int64_t total = 0;
+            for (const auto& g : P.groups) total += g.items;
+            if (total >= kTargetItems) break;
+            changed = false;
+            for (auto& g : P.groups) {
+                const int floor_ell = std::min(walk_bits(g.n, g.nw), 5);
+                if (tune_get((int)field, g.n) > 0 || g.ell <= floor_ell) continue;
+                g.ell -= 1;
+                g.log2_chunks += 1;
+                g.items <<= 1;
+                changed = true;
+            }
+        }
+        part_off = 0;
+        for (auto& g : P.groups) {
+            const int lg = group_log2(g.log2_chunks, chunks_per_warp(false, false, g.n));
+            g.partials_per_mat = (int64_t)1 << (g.log2_chunks - lg);
+            g.part_off = part_off;
+            part_off += g.partials_per_mat * (int64_t)g.mats.size();
+        }
+    }
     P.col_elems = col_off;
     P.total_partials = part_off;
     P.batch = batch;

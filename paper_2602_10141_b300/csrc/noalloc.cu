@@ -183,6 +183,8 @@ extern "C" int perm_modp_noalloc(const uint32_t* A, const int32_t* n, const int6
         L.mat_stride = (int64_t)(nn + 1) * pad4(nn);
         const int bits = walk_bits(nn, 1);   // Nijenhuis-Wilf form: 2^(nn-1) Gray steps
         L.ell = chunk_log2_modp(bits);
+        // exact arithmetic: shorter chunks when the run is too small to fill the GPU
+        while (L.ell > (bits < 5 ? bits : 5) && ((int64_t)(k1 - k0) << (bits - L.ell)) < ((int64_t)1 << 18)) --L.ell;
         L.log2_chunks = bits - L.ell;
         L.item_begin = 0;
         L.item_end = (uint64_t)(k1 - k0) << L.log2_chunks;
