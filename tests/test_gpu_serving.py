@@ -246,3 +246,55 @@ def test_drain_reports_timeout_then_completes(px):
         assert res[t][0] == _batched(px, A, 2, p)
     finally:
         S.close()
+
+
+def _block_diag(blocks):
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n), dtype=blocks[0].dtype)
+    o = 0
+    for b in blocks:
+        k = b.shape[0]
+        M[o:o + k, o:o + k] = b
+        o += k
+    return M
+
+
+def test_max_size_requests_served_with_small_ones(px):
+    """The largest float (n = 32, complex) and a large F_p request (n = 40)
+    served beside small requests: block-diagonal matrices with rows and
+    columns shuffled, so the oracle's value is the product of the blocks'
+    permanents; the served results also equal the batched path's."""
+    g = rng(5000)
+    S = Server(px)
+    try:
+        cb = [ensemble("haar_u", 8, 1, seed=5000 + k)[0] for k in range(4)]
+        C = _block_diag(cb)
+        P, Q = g.permutation(32), g.permutation(32)
+        C = np.ascontiguousarray(C[P][:, Q])
+        c_ref = np.prod([O.perm_dp(b) for b in cb])
+        p = 2147483629
+        mb = [random_residues(10, p, g) for _ in range(4)]
+        M = _block_diag(mb).astype(np.uint32)
+        P, Q = g.permutation(40), g.permutation(40)
+        M = np.ascontiguousarray(M[P][:, Q])
+        m_ref = 1
+        for b in mb:
+            m_ref = m_ref * O.perm_modp_dp(b, p) % p
+        small = [ensemble("goe", 11, 1, seed=5100 + i)[0] for i in range(8)]
+        rc, tc = S.submit(C, 0)
+        assert rc == 0, px.last_error()
+        rc, tm = S.submit(M, 2, p)
+        assert rc == 0, px.last_error()
+        ts = []
+        for A in small:
+            rc, t = S.submit(A, 1)
+            assert rc == 0
+            ts.append((t, 1))
+        res = S.wait([(tc, 0), (tm, 2)] + ts, timeout=300.0)
+        assert abs(res[tc][0] - c_ref) <= 1e-9 * abs(c_ref), (res[tc][0], c_ref)
+        assert res[tc][0] == _batched(px, C, 0)
+        assert res[tm][0] == m_ref
+        for A, (t, _) in zip(small, ts):
+            assert res[t][0] == _batched(px, A, 1)
+    finally:
+        S.close()
