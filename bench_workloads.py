@@ -74,8 +74,17 @@ def schur_long(args):
     import tempfile
 
     import paper_2602_10141_b300 as px
+    import oracle as O
     ns = [int(x) for x in args.ns.split(",")] if args.ns else list(range(36, 44))
     tmp = args.ckpt_dir or tempfile.mkdtemp(prefix="permx_schur_")
+    # the oracle's F_p Ryser (row sums recomputed per subset) on 2^22 Gray indices of S_n
+    # for the first n, on the host cores: the rate the per-n extrapolations use
+    n0 = ns[0]
+    p0 = O.primes_1_mod_n(n0, 1)[0]
+    S0 = O.schur_residue_matrix(n0, p0, O.primitive_nth_root(p0, n0))
+    t0 = time.perf_counter()
+    O.ryser_modp_gray_range(S0, p0, 1 << 30, (1 << 30) + (1 << 22))
+    oracle_rate = n0 * (1 << 22) / (time.perf_counter() - t0)
     os.makedirs(tmp, exist_ok=True)
     for n in ns:
         ck = os.path.join(tmp, f"s{n}.ckpt")
@@ -97,6 +106,9 @@ def schur_long(args):
         print(json.dumps({"workload": "schur_long", "n": n, "perm_S_n": str(value), "seconds": dt,
                           "primes": primes, "residues": residues, "check_prime": primes[-1],
                           "resumed": resumed,   # seconds and rates then cover this call's share only
+                          "cpu_baseline": {"value": oracle_rate, "unit": "terms/s", "cores": O.num_threads(),
+                                           "kind": "oracle", "sample": f"2^22 Gray indices of S_{n0} mod {p0}",
+                                           "extrapolated_s": terms * 2 / oracle_rate},
                           "evaluated_terms_per_s": None if resumed else terms / dt,
                           "nominal_terms_per_s": None if resumed else 2 * terms / dt,
                           "bound_ok": value * value <= n ** n}), flush=True)
@@ -304,8 +316,10 @@ def ensembles_batched(args):
     step()
     torch.cuda.synchronize()
 
-    # oracle check on a seeded subsample (n <= 20)
+    # oracle check on a seeded subsample (n <= 16), and the oracle's Ryser rate
+    # (double-double, row sums recomputed per subset) timed on it
     worst_rel, checked = 0.0, 0
+    oracle_terms, oracle_s = 0.0, 0.0
     for cplx, (flat, ns, offs, out) in fields.items():
         got = out.cpu().numpy()
         host = flat.cpu().numpy()
@@ -316,17 +330,26 @@ def ensembles_batched(args):
                 continue
             A = host[offs[i]:offs[i] + n * n].reshape(n, n)
             ref = O.perm_dp(A)
+            t_o = time.perf_counter()
             _, abs_terms = O.perm_ryser(A, with_abs=True)
+            oracle_s += time.perf_counter() - t_o
+            oracle_terms += n * 2.0 ** n
             err = abs(got[i] - ref)
             assert err <= max(1e-9 * abs(ref), 64 * n * 2.0 ** -53 * abs_terms), (cplx, n, got[i], ref)
             worst_rel = max(worst_rel, err / abs(ref))
             checked += 1
+    oracle_rate = oracle_terms / max(oracle_s, 1e-9)
     line = {"workload": "ensembles_batched", "metric": "perms_per_s", "value": total_perms / t, "unit": "perm/s",
             "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "nominal_terms_per_s": total_terms / t, "perms_per_step": total_perms,
             "plain_perms_per_s": plain_perms / (plain_ms / 1e3),
             "plain_nominal_terms_per_s": plain_terms / (plain_ms / 1e3),
-            "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel, "dtype": "c128+f64",
+            "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel,
+            "cpu_baseline": {"value": oracle_rate, "unit": "terms/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"Ryser in double-double on the {checked} checked matrices (n <= 16), "
+                                       "n 2^n terms each",
+                             "extrapolated_s_per_step": total_terms / oracle_rate},
+            "dtype": "c128+f64",
             "data": "synthetic, generated on the device (seeded torch generators)",
             "config": {"sizes": list(SIZES), "per_size_and_ensemble": count, "scale_of_50000": args.scale,
                        "complex128": list(CPLX), "float64": list(REAL)}}
