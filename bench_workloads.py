@@ -63,6 +63,8 @@ def run(args):
         return profile_stats(args)
     if args.workload == "batch_scaling":
         return batch_scaling(args)
+    if args.workload == "orthogonal_large":
+        return orthogonal_large(args)
     raise ValueError(args.workload)
 
 
@@ -130,6 +132,37 @@ def profile_fp(args):
             (px.perm_c128 if cplx else px.perm_f64)(A, [20] * 64, [i * 400 for i in range(64)], out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "64 x n=20 complex + 64 x n=20 real Ginibre", "arith": px.permx_get_fp_arith()}))
+    return 0
+
+
+def orthogonal_large(args):
+    """Table "orthogonal" (paper §5.1) with 10^6 Haar O(n) per n instead of 50,000:
+    four seeded blocks of 250,000, each through one batched float64 call and the
+    device statistics; the mean over blocks and its standard error are reported."""
+    import torch
+
+    import paper_2602_10141_b300 as px
+    from workloads.device import batch
+    orth, _, _ = _paper_tables()
+    rows = []
+    t_start = time.perf_counter()
+    block, nblocks = 250_000, 4
+    for n, (var, kurt) in orth.items():
+        vs, ks = [], []
+        walk_ms = 0.0
+        for b in range(nblocks):
+            v, ms = _perm_batch(px, torch, "haar_o", n, block, 7000 + 97 * n + b)
+            walk_ms += ms
+            s = px.perm_sample_stats(v)
+            vs.append(s["var_re"])
+            ks.append(s["exkurt_re"])
+            del v
+        se = lambda x: statistics.stdev(x) / math.sqrt(len(x))   # noqa: E731
+        rows.append({"n": n, "samples": block * nblocks, "var": statistics.mean(vs), "var_se": se(vs),
+                     "paper_var": var, "exkurt": statistics.mean(ks), "exkurt_se": se(ks), "paper_exkurt": kurt,
+                     "walk_s": walk_ms / 1e3})
+    print(json.dumps({"workload": "orthogonal_large", "rows": rows, "wall_s": time.perf_counter() - t_start}),
+          flush=True)
     return 0
 
 
