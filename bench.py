@@ -218,7 +218,8 @@ def main():
                     help="small case for ncu: the same kernel over 2^30 Gray indices of S_33 mod one prime")
     ap.add_argument("--workload", default="schur33",
                     choices=["schur33", "haar14_plain", "ensembles_batched", "serving", "profile_fp", "schur_long",
-                             "paper_tables", "profile_stats", "batch_scaling", "orthogonal_large"],
+                             "paper_tables", "profile_stats", "batch_scaling", "orthogonal_large",
+                             "lognormal_large"],
                     help="schur33 is the headline; the others measure the plain, batched and served paths")
     ap.add_argument("--ns", default="", help="schur_long: comma-separated n (default 36..43)")
     ap.add_argument("--ckpt-dir", default="", help="schur_long: keep checkpoints here (resume from them)")
