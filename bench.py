@@ -223,6 +223,8 @@ def main():
                     help="schur33 is the headline; the others measure the plain, batched and served paths")
     ap.add_argument("--ns", default="", help="schur_long: comma-separated n (default 36..43)")
     ap.add_argument("--ckpt-dir", default="", help="schur_long: keep checkpoints here (resume from them)")
+    ap.add_argument("--disjoint", action="store_true",
+                    help="schur_long: use primes disjoint from the default set (a cross-check of a long run)")
     ap.add_argument("--max-slices", type=int, default=0,
                     help="schur_long: stop after this many checkpointed slices per n (0 = run to the end)")
     ap.add_argument("--scale", type=float, default=0.02,

@@ -95,7 +95,20 @@ def schur_long(args):
         resumed = os.path.exists(ck)
         t0 = time.perf_counter()
         try:
-            value, primes, residues = px.perm_schur_crt_ex(n, 0, ck, max_slices=args.max_slices)
+            if args.disjoint:
+                # the primes just below the default set: the fewest whose product exceeds
+                # 2 n^(n/2) (checked exactly, squared), plus one more as the check prime
+                k_default = px._lib.perm_schur_prime_count(n)
+                skip = k_default + 1
+                cand = px.perm_primes_1_mod_n(n, 24, skip=skip)
+                prod, k = 1, 0
+                while prod * prod <= 4 * n ** n:
+                    prod *= cand[k]
+                    k += 1
+                primes = cand[:k + 1]
+                value, residues = px.perm_schur_crt_primes(n, primes, ck, max_slices=args.max_slices)
+            else:
+                value, primes, residues = px.perm_schur_crt_ex(n, 0, ck, max_slices=args.max_slices)
         except px.PermxError as e:
             if e.code != px.PERMX_EAGAIN:
                 raise

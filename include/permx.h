@@ -244,6 +244,17 @@ int perm_schur_crt_ex(int32_t n, int32_t nprimes, const char* ckpt_path, uint64_
                       int64_t max_slices, int64_t out_i128[2], char* out_dec, size_t out_dec_len,
                       uint32_t* residues_out, uint32_t* primes_out);
 
+/* perm(S_n) with the caller's primes: primes[0..count-2] for the CRT and
+ * primes[count-1] as the check prime (2 <= count <= PERMX_MAX_PRIMES; each an
+ * odd prime below 2^31 with p = 1 (mod n), all distinct, and the product of
+ * the first count-1 above 2 n^(n/2); PERMX_EINVAL otherwise, before any GPU
+ * work).  For example a second, disjoint prime set cross-checks a long run.
+ * Checkpoint, slicing, outputs and errors as perm_schur_crt_ex; residues_out
+ * (host, may be NULL) receives count residues. */
+int perm_schur_crt_primes(int32_t n, const uint32_t* primes, int32_t count, const char* ckpt_path,
+                          uint64_t slice_subsets, int64_t max_slices, int64_t out_i128[2], char* out_dec,
+                          size_t out_dec_len, uint32_t* residues_out);
+
 /* ------------------------------------------------------------------------
  * Host-side field and CRT helpers (paper §2.1); no GPU needed.
  * ---------------------------------------------------------------------- */

@@ -59,6 +59,8 @@ def _load() -> ctypes.CDLL:
         "perm_schur_crt": ([i32, i32, ctypes.c_char_p, P(i64), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "perm_schur_crt_ex": ([i32, i32, ctypes.c_char_p, u64, i64, P(i64), ctypes.c_char_p, ctypes.c_size_t,
                                P(u32), P(u32)], ctypes.c_int),
+        "perm_schur_crt_primes": ([i32, P(u32), i32, ctypes.c_char_p, u64, i64, P(i64), ctypes.c_char_p,
+                                   ctypes.c_size_t, P(u32)], ctypes.c_int),
         "perm_primes_1_mod_n": ([i32, i32, i32, P(u32)], ctypes.c_int),
         "perm_primitive_root": ([u32, i32, P(u32)], ctypes.c_int),
         "perm_schur_residues": ([i32, u32, u32, P(u32)], ctypes.c_int),
@@ -335,6 +337,18 @@ def perm_schur_crt_ex(n: int, nprimes: int = 0, ckpt_path: str | None = None, sl
     _check(rc)
     k = int(np.count_nonzero(pr))
     return int(buf.value.decode()), [int(x) for x in pr[:k]], [int(x) for x in res[:k]]
+
+
+def perm_schur_crt_primes(n: int, primes, ckpt_path: str | None = None, slice_subsets: int = 0,
+                          max_slices: int = 0):
+    """perm(S_n) with the given primes (the last one checks); returns (value, residues)."""
+    pp = _u32(primes)
+    buf = ctypes.create_string_buffer(512)
+    res = np.zeros(len(pp), np.uint32)
+    _check(_lib.perm_schur_crt_primes(n, _p(pp, ctypes.c_uint32), len(pp),
+                                      ckpt_path.encode() if ckpt_path else None, slice_subsets, max_slices, None,
+                                      buf, len(buf), _p(res, ctypes.c_uint32)))
+    return int(buf.value.decode()), [int(x) for x in res]
 
 
 def perm_primes_1_mod_n(n: int, count: int, skip: int = 0) -> list[int]:

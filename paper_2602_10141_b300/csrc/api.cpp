@@ -174,13 +174,42 @@ int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, 
     return rc;
 }
 
+}  // extern "C"
+
+namespace permx {
+static int schur_outputs(int rc, const SchurResult& res, int64_t out_i128[2], char* out_dec, size_t out_dec_len,
+                         uint32_t* residues_out, uint32_t* primes_out);
+}  // namespace permx
+
+extern "C" {
+
+int perm_schur_crt_primes(int32_t n, const uint32_t* primes, int32_t count, const char* ckpt_path,
+                          uint64_t slice_subsets, int64_t max_slices, int64_t out_i128[2], char* out_dec,
+                          size_t out_dec_len, uint32_t* residues_out) {
+    clear_error();
+    if (!out_i128 && !out_dec) return fail(PERMX_EINVAL, "no output buffer");
+    if (!primes || count < 2 || count > PERMX_MAX_PRIMES) return fail(PERMX_EINVAL, "need 2..64 primes");
+    SchurResult res;
+    const std::vector<uint32_t> pv(primes, primes + count);
+    const int rc = schur_crt_run_primes(n, pv, ckpt_path, slice_subsets, max_slices, res);
+    return schur_outputs(rc, res, out_i128, out_dec, out_dec_len, residues_out, nullptr);
+}
+
 int perm_schur_crt_ex(int32_t n, int32_t nprimes, const char* ckpt_path, uint64_t slice_subsets, int64_t max_slices,
                       int64_t out_i128[2], char* out_dec, size_t out_dec_len, uint32_t* residues_out,
                       uint32_t* primes_out) {
     clear_error();
     if (!out_i128 && !out_dec) return fail(PERMX_EINVAL, "no output buffer");
     SchurResult res;
-    int rc = schur_crt_run(n, nprimes, ckpt_path, slice_subsets, max_slices, res);
+    const int rc = schur_crt_run(n, nprimes, ckpt_path, slice_subsets, max_slices, res);
+    return schur_outputs(rc, res, out_i128, out_dec, out_dec_len, residues_out, primes_out);
+}
+
+}  // extern "C"
+
+namespace permx {
+static int schur_outputs(int rc, const SchurResult& res, int64_t out_i128[2], char* out_dec, size_t out_dec_len,
+                         uint32_t* residues_out, uint32_t* primes_out) {
     if (residues_out)
         for (size_t i = 0; i < res.residues.size(); ++i) residues_out[i] = res.residues[i];
     if (primes_out)
@@ -201,6 +230,9 @@ int perm_schur_crt_ex(int32_t n, int32_t nprimes, const char* ckpt_path, uint64_
     }
     return PERMX_OK;
 }
+}  // namespace permx
+
+extern "C" {
 
 int perm_schur_crt(int32_t n, int32_t nprimes, const char* ckpt_path, int64_t out_i128[2], char* out_dec,
                    size_t out_dec_len) {

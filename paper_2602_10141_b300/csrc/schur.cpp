@@ -180,6 +180,22 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
     const int k = nprimes ? nprimes : schur_prime_count(n);
     std::vector<uint32_t> primes(k + 1);
     if (primes_1_mod_n(n, k + 1, 0, primes.data()) != k + 1) return fail(PERMX_EINVAL, "not enough primes");
+    return schur_crt_run_primes(n, primes, ckpt_path, slice_subsets, max_slices, res);
+}
+
+int schur_crt_run_primes(int n, const std::vector<uint32_t>& primes, const char* ckpt_path, uint64_t slice_subsets,
+                         int64_t max_slices, SchurResult& res) {
+    if (n < 1 || n > PERMX_MAX_N_MODP) return fail(PERMX_EINVAL, "n outside [1, 48]");
+    if (primes.size() < 2 || primes.size() > (size_t)PERMX_MAX_PRIMES)
+        return fail(PERMX_EINVAL, "need 2..64 primes (the last one checks)");
+    for (size_t i = 0; i < primes.size(); ++i) {
+        const uint32_t p = primes[i];
+        if (p <= 2 || p >= (1u << 31) || !is_prime_u32(p) || p % (uint32_t)n != 1 % (uint32_t)n)
+            return fail(PERMX_EINVAL, "prime " + std::to_string(p) + " is not an odd prime below 2^31 with p = 1 (mod n)");
+        for (size_t j = 0; j < i; ++j)
+            if (primes[j] == p) return fail(PERMX_EINVAL, "repeated prime " + std::to_string(p));
+    }
+    const int k = (int)primes.size() - 1;
     if (!modulus_suffices(n, primes.data(), k))
         return fail(PERMX_EINVAL, "product of " + std::to_string(k) + " primes does not exceed 2 n^(n/2)");
 

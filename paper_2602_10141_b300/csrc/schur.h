@@ -50,5 +50,8 @@ int write_checkpoint(const std::string& path, const SchurState& st);
 int read_checkpoint(const std::string& path, SchurState& st);
 int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subsets, int64_t max_slices,
                   SchurResult& res);
+// the same with the caller's primes (the last one is the check prime)
+int schur_crt_run_primes(int n, const std::vector<uint32_t>& primes, const char* ckpt_path, uint64_t slice_subsets,
+                         int64_t max_slices, SchurResult& res);
 
 }  // namespace permx

@@ -117,3 +117,15 @@ def test_chunk_tuning_table_host_logic(px):
         px.perm_tune_set(px.FIELD_C128, 20, 0)
         px.perm_tune_set(px.FIELD_MODP, 40, 0)
     assert px.perm_tune_get(px.FIELD_C128, 20) == default
+
+
+def test_schur_crt_primes_argument_checks(px):
+    """perm_schur_crt_primes rejects bad prime lists on the host, before any GPU work."""
+    n = 23
+    good = O.primes_1_mod_n(n, 6)
+    for bad, what in (([good[0]], "need 2"), ([good[0], good[0], good[1]], "repeated"),
+                      ([good[0], 2147483647], "not an odd prime"), ([4] + good[:2], "not an odd prime"),
+                      (good[:2], "does not exceed")):
+        with pytest.raises(px.PermxError):
+            px.perm_schur_crt_primes(n, bad)
+        assert what in px.last_error(), (bad, px.last_error())

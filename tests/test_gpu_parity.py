@@ -390,3 +390,18 @@ def test_schur_crt_matches_oracle_fixture(px):
     for r in rows:
         n, value = int(r[0]), int(r[1])
         assert px.perm_schur_crt(n) == value, n
+
+
+def test_schur_crt_disjoint_primes_match_fixture(px):
+    """perm_schur_crt_primes with primes disjoint from the default set (the
+    next ones down) gives the oracle's perm(S_n) for n = 23, 25, 27."""
+    from conftest import read_golden
+    rows = {int(r[0]): (int(r[1]), [int(x) for x in r[2:]]) for r in read_golden("schur_crt_oracle.txt")}
+    for n in (23, 25, 27):
+        value, used = rows[n]
+        k = len(used) - 1
+        disjoint = O.primes_1_mod_n(n, k + 1, below=min(used))
+        assert not set(disjoint) & set(used)
+        got, residues = px.perm_schur_crt_primes(n, disjoint)
+        assert got == value, n
+        assert residues[-1] == value % disjoint[-1]
