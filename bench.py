@@ -130,7 +130,7 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(primes, mats, target_s: float = 12.0):
+def cpu_baseline(primes, mats, target_s: float = 16.0):
     """The oracle's Ryser evaluation (row sums recomputed for every subset) on a
     bounded Gray-index range of the first prime's matrix, timed on the host."""
     import oracle as O
