@@ -675,7 +675,14 @@ def paper_tables(args):
         thr = math.factorial(n) / n ** n / n ** 2
         s = px.perm_sample_stats(v, threshold=thr, real_tol=1e-9)
         mu = math.factorial(n) * math.factorial(n - 1) / math.factorial(2 * n - 1)
+        # exponential law (paper eq. "exp"): empirical CDF of |perm|^2 / mu from a device
+        # histogram on geometric edges against 1 - exp(-x)
+        tq = np.geomspace(1e-3, 12.0, 64)
+        h = px.perm_sample_histogram(v, tq * mu, px.HIST_ABS2)
+        ecdf = np.cumsum(h)[:-1] / N
+        cdf_dev = float(np.max(np.abs(ecdf - (1.0 - np.exp(-tq)))))
         rows.append({"n": n, "mean_abs2": s["mean_abs2"], "exact_m2": mu, "paper_sigma2": math.factorial(n) / n ** n,
+                     "max_cdf_dev_vs_exponential": cdf_dev,
                      "m4_over_m2sq": s["mean_abs4"] / s["mean_abs2"] ** 2,
                      "pseudo_cov": math.hypot(s["mean_z2_re"], s["mean_z2_im"]) / s["mean_abs2"],
                      "pr_above_paper_threshold": s["count_above"] / N, "exponential_law": math.exp(-thr / mu)})

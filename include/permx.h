@@ -351,6 +351,24 @@ typedef struct {
 int perm_sample_stats(int field, const void* values, int64_t count, double threshold, double real_tol,
                       perm_stats_t* out, void* stream);
 
+/* Histogram of |z|^2 (PERMX_HIST_ABS2, formed as in perm_sample_stats), Re z
+ * (PERMX_HIST_RE) or Im z (PERMX_HIST_IM) over the `count` device values:
+ * edges = HOST array of nedges strictly increasing doubles (1..4097);
+ * counts = DEVICE int64 array of nedges + 1, overwritten: counts[0] values
+ * below edges[0], counts[b] values in [edges[b-1], edges[b]), counts[nedges]
+ * values at or above edges[nedges-1]; a value whose selected quantity is NaN
+ * is not counted (NaN + 0i counts in the Im histogram as 0).  A value
+ * equal to an edge goes to the bin that edge opens.  Edges spaced in
+ * geometric progression on |z|^2 bin log|z| without taking a logarithm.
+ * Asynchronous on `stream` (the edges are copied during the call).
+ * Errors: EINVAL (field MODP, bad kind, NULL or misaligned pointer, bad
+ * edges, count < 0), ENOMEM, ECUDA. */
+#define PERMX_HIST_ABS2 0
+#define PERMX_HIST_RE 1
+#define PERMX_HIST_IM 2
+int perm_sample_histogram(int field, const void* values, int64_t count, int kind, const double* edges,
+                          int32_t nedges, int64_t* counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

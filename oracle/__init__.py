@@ -23,6 +23,8 @@ What it computes, and where the paper defines it:
   ``c_m = #{sigma : sum_i i*sigma(i) = m (mod n)}`` reduced modulo the
   cyclotomic polynomial ``Phi_n`` (definition of ``S_n``, paper §1).
 
+* ``sample_histogram`` — counts of |z|^2, Re z or Im z between given edges
+  (the distributions behind the paper's Q-Q plots and tail probabilities).
 * ``sample_stats`` — the sample moments, counts and extremes the paper
   reports over batches of permanents (§3.2 second moment and circularity, §5.1
   Table "orthogonal", §6.1 real-valuedness, §7.2 Table "lognormal", the
@@ -498,4 +500,21 @@ def sample_stats(values, threshold: float = math.inf, real_tol: float = 0.0) -> 
             out["log_exkurt"] = float(np.float64(fs(dl ** 4) / M) / np.float64(lv) ** 2 - 3.0)
         else:
             out.update(log_mean=math.nan, log_var=math.nan, log_skew=math.nan, log_exkurt=math.nan)
+    return out
+
+
+def sample_histogram(values, edges, kind: int = 0) -> np.ndarray:
+    """Counts of x = |z|^2 (kind 0; re*re + im*im, each product and the sum
+    rounded to double), Re z (1) or Im z (2) against sorted edges: element 0
+    counts x < edges[0], element b counts edges[b-1] <= x < edges[b], the last
+    x >= edges[-1]; NaN is not counted."""
+    z = np.asarray(values)
+    re = np.asarray(z.real, dtype=np.float64).reshape(-1)
+    im = np.asarray(z.imag, dtype=np.float64).reshape(-1) if np.iscomplexobj(z) else np.zeros_like(re)
+    x = re * re + im * im if kind == 0 else (re if kind == 1 else im)
+    x = x[~np.isnan(x)]
+    e = np.asarray(edges, dtype=np.float64)
+    out = np.zeros(len(e) + 1, np.int64)
+    for v in x:                                    # plain definition: count the edges at or below v
+        out[int(np.sum(e <= v))] += 1
     return out

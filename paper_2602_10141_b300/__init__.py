@@ -77,6 +77,8 @@ def _load() -> ctypes.CDLL:
         "permx_get_fp_arith": ([], ctypes.c_int),
         "perm_c128_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
         "perm_f64_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
+        "perm_sample_histogram": ([ctypes.c_int, vp, i64, ctypes.c_int, P(ctypes.c_double), i32, vp, vp],
+                                  ctypes.c_int),
         "perm_sample_stats": ([ctypes.c_int, vp, i64, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         "permx_peak_probe": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                               P(ctypes.c_double)], ctypes.c_int),
@@ -172,6 +174,27 @@ def perm_gather(U, rows, cols, out, stream=None):
     _check(f(U.data_ptr(), U.shape[0], U.stride(0), _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
              rows.shape[1], rows.shape[0], out.data_ptr(), _stream(stream)))
     return out
+
+
+HIST_ABS2, HIST_RE, HIST_IM = 0, 1, 2
+
+
+def perm_sample_histogram(values, edges, kind: int = 0, stream=None):
+    """Counts of |z|^2 (kind 0), Re z (1) or Im z (2) over sorted host `edges`:
+    a numpy int64 array of len(edges) + 1 (below, bins, at-or-above).  Synchronises."""
+    import torch
+    if values.dtype == torch.complex128:
+        field = FIELD_C128
+    elif values.dtype == torch.float64:
+        field = FIELD_F64
+    else:
+        raise TypeError("values must be complex128 or float64")
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    counts = torch.empty(len(e) + 1, dtype=torch.int64, device=values.device)
+    _check(_lib.perm_sample_histogram(field, values.data_ptr(), values.numel(), kind, _p(e, ctypes.c_double),
+                                      len(e), counts.data_ptr(), _stream(stream)))
+    torch.cuda.synchronize(values.device)
+    return counts.cpu().numpy()
 
 
 class PermStats(ctypes.Structure):

@@ -1,4 +1,5 @@
-// Sample statistics of a batch of permanents (perm_sample_stats): the
+// Sample statistics of a batch of permanents (perm_sample_stats, and
+// perm_sample_histogram over caller-supplied edges): the
 // distributional measurements of paper §3-§7 taken over the batched output
 // without copying it to the host.
 //
@@ -210,10 +211,83 @@ __global__ void __launch_bounds__(kT) stats_final_kernel(const double* __restric
     *out = r;
 }
 
+// Histogram over caller-supplied edges (sorted, in shared memory): bin b holds
+// edges[b] <= x < edges[b+1]; counts[0] is below edges[0], counts[nedges] at or
+// above the last edge; NaN is not counted.  Integer counts: any order gives the
+// same result.
+constexpr int kMaxEdges = 4097;
+__global__ void __launch_bounds__(kT) hist_kernel(const double* __restrict__ v, int cplx, int64_t count, int kind,
+                                                  const double* __restrict__ edges, int nedges,
+                                                  unsigned long long* __restrict__ counts) {
+    extern __shared__ unsigned char smem[];
+    double* se = reinterpret_cast<double*>(smem);
+    unsigned int* sc = reinterpret_cast<unsigned int*>(se + nedges);
+    for (int i = threadIdx.x; i < nedges; i += kT) se[i] = edges[i];
+    for (int i = threadIdx.x; i <= nedges; i += kT) sc[i] = 0u;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kT;
+    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < count; i += stride) {
+        double re, im;
+        load_value(v, cplx, i, re, im);
+        const double x = kind == PERMX_HIST_ABS2 ? abs2_rn(re, im) : (kind == PERMX_HIST_RE ? re : im);
+        if (x != x) continue;
+        int lo = 0, hi = nedges;               // first edge > x, by bisection: bin = that index
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (se[mid] <= x) lo = mid + 1;
+            else hi = mid;
+        }
+        atomicAdd(&sc[lo], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= nedges; i += kT)
+        if (sc[i]) atomicAdd(&counts[i], (unsigned long long)sc[i]);
+}
+
 }  // namespace
 }  // namespace permx
 
 using namespace permx;
+
+extern "C" int perm_sample_histogram(int field, const void* values, int64_t count, int kind, const double* edges,
+                                     int32_t nedges, int64_t* counts, void* stream) {
+    clear_error();
+    if (field != PERMX_FIELD_C128 && field != PERMX_FIELD_F64)
+        return fail(PERMX_EINVAL, "histograms take complex128 or float64 values");
+    if (!edges || !counts || (!values && count > 0)) return fail(PERMX_EINVAL, "NULL argument");
+    if (count < 0) return fail(PERMX_EINVAL, "negative count");
+    if (kind != PERMX_HIST_ABS2 && kind != PERMX_HIST_RE && kind != PERMX_HIST_IM)
+        return fail(PERMX_EINVAL, "unknown histogram quantity");
+    if (nedges < 1 || nedges > kMaxEdges) return fail(PERMX_EINVAL, "need 1..4097 edges");
+    for (int i = 0; i < nedges; ++i) {
+        if (!(edges[i] == edges[i]) || (i > 0 && !(edges[i - 1] < edges[i])))
+            return fail(PERMX_EINVAL, "edges must be strictly increasing and not NaN");
+    }
+    if (reinterpret_cast<uintptr_t>(values) % (field == PERMX_FIELD_C128 ? 16 : 8) ||
+        reinterpret_cast<uintptr_t>(counts) % 8)
+        return fail(PERMX_EINVAL, "misaligned values or counts");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PERMX_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * (size_t)(nedges + 1), s));
+    if (count == 0) return PERMX_OK;
+    void* d_edges = nullptr;
+    PERMX_CUDA(ws_alloc(&d_edges, sizeof(double) * (size_t)nedges, s));
+    cudaError_t e = cudaMemcpyAsync(d_edges, edges, sizeof(double) * (size_t)nedges, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const size_t shmem = sizeof(double) * (size_t)nedges + sizeof(unsigned int) * (size_t)(nedges + 1);
+        if (shmem > 48 * 1024) e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)shmem);
+        if (e == cudaSuccess) {
+            hist_kernel<<<grid_for(count), kT, shmem, s>>>(static_cast<const double*>(values),
+                                                            field == PERMX_FIELD_C128, count, kind,
+                                                            static_cast<const double*>(d_edges), nedges,
+                                                            reinterpret_cast<unsigned long long*>(counts));
+            e = cudaGetLastError();
+        }
+    }
+    ws_free(d_edges, s);
+    if (e != cudaSuccess) return cuda_fail(e, "perm_sample_histogram");
+    return PERMX_OK;
+}
 
 extern "C" int perm_sample_stats(int field, const void* values, int64_t count, double threshold, double real_tol,
                                  perm_stats_t* out, void* stream) {

@@ -154,6 +154,13 @@ def test_haar_unitary_second_moment_and_circularity(px, n):
     if n == 17:
         assert abs(frac - 0.18) <= 0.015                 # paper §7: 18 % at n = 17
     assert s["count_real"] <= 0.01 * N_SAMPLES          # a generic complex permanent is not real
+    # the exponential law itself: empirical CDF of |perm U|^2 / mu (device histogram on
+    # geometric edges) within a few 1/sqrt(N) of 1 - exp(-x)
+    tq = np.geomspace(1e-3, 12.0, 64)
+    h = px.perm_sample_histogram(v, tq * mu, px.HIST_ABS2)
+    assert h.sum() == N_SAMPLES
+    dev = np.max(np.abs(np.cumsum(h)[:-1] / N_SAMPLES - (1.0 - np.exp(-tq))))
+    assert dev <= (0.03 if n == 7 else 0.015), dev
 
 
 # paper §5.1, Table "orthogonal" (tests/golden/orthogonal_table.txt): n, Var[perm(O)], excess kurtosis;
@@ -215,3 +222,42 @@ def test_gaussian_anticoncentration(px, name):
         fracs.append(s["count_above"] / count)
     assert 0.65 <= fracs[-1] <= 0.99, fracs
     assert all(b > a for a, b in zip(fracs, fracs[1:])), fracs
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_histogram_parity_with_oracle(px, kind):
+    """perm_sample_histogram equals the oracle's counts exactly: linear and
+    geometric edges, values placed exactly on edges, NaN entries, a ragged count."""
+    import torch
+    g = rng(600 + kind)
+    count = 200_003
+    v = g.normal(0.0, 1.0, count) + 1j * g.normal(0.0, 1.0, count)
+    edges_lin = np.linspace(-3.0, 3.0, 61)
+    edges_geo = np.geomspace(1e-4, 30.0, 129)          # |z|^2 on a log scale
+    edges = edges_geo if kind == 0 else edges_lin
+    v[:50] = edges[10:60] if kind != 2 else 1j * edges[10:60]   # exactly on edges (|z|^2 for kind 0 below)
+    if kind == 0:
+        v[:50] = np.sqrt(edges[10:60])                 # |z|^2 = rn(x*x) may differ from the edge by an ulp
+    v[50:53] = complex(np.nan, np.nan)
+    v[53] = complex(np.nan, 0.5)                       # NaN only in Re: still counted for Im
+    ref = O.sample_histogram(v, edges, kind)
+    got = px.perm_sample_histogram(torch.from_numpy(v).cuda(), edges, kind)
+    assert list(got) == list(ref)
+    assert got.sum() == count - (3 if kind == 2 else 4)
+    # float64 values: Im = 0
+    r = v.real.copy()
+    got_r = px.perm_sample_histogram(torch.from_numpy(r).cuda(), edges_lin, 1)
+    assert list(got_r) == list(O.sample_histogram(r, edges_lin, 1))
+
+
+def test_histogram_argument_errors(px):
+    import torch
+    v = torch.zeros(4, dtype=torch.complex128, device="cuda")
+    with pytest.raises(px.PermxError):
+        px.perm_sample_histogram(v, [1.0, 1.0])            # not strictly increasing
+    with pytest.raises(px.PermxError):
+        px.perm_sample_histogram(v, [0.0, np.nan])
+    with pytest.raises(px.PermxError):
+        px.perm_sample_histogram(v, [0.0, 1.0], kind=3)
+    got = px.perm_sample_histogram(v[:0], [0.0, 1.0])       # empty input: all zero
+    assert list(got) == [0, 0, 0]

@@ -102,3 +102,39 @@ def test_planted_stats_mistake_is_caught(name, old, new):
     exec(src.replace(old, new), ns)
     failed = [n for n, ok in _pins(ns["sample_stats"]) if not ok]
     assert failed, f"planted mistake '{name}' passed every pin"
+
+
+def test_sample_histogram_pins():
+    """Counts on exact edges, below and above, NaN skipped, |z|^2 and Re / Im
+    selected; the total equals the non-NaN count; numpy's histogram on the
+    interior bins agrees."""
+    edges = [0.0, 0.25, 1.0, 4.0]
+    z = np.array([0.5, -0.5, 0.25, 0.0, 3 + 4j, 0.5j, -2.0, 1.0, np.nan, 2j])
+    # |z|^2: 0.25, 0.25, 0.0625, 0, 25, 0.25, 4, 1, nan, 4
+    assert list(O.sample_histogram(z, edges, 0)) == [0, 2, 3, 1, 3]
+    # Re z: 0.5, -0.5, 0.25, 0, 3, 0, -2, 1, (nan: skipped), 0
+    assert list(O.sample_histogram(z, edges, 1)) == [2, 3, 2, 2, 0]
+    # Im z: 0, 0, 0, 0, 4, 0.5, 0, 0, 0 (the NaN entry has imaginary part 0), 2
+    assert list(O.sample_histogram(z, edges, 2)) == [0, 7, 1, 1, 1]
+    g = np.random.default_rng(3)
+    v = g.normal(size=5000) + 1j * g.normal(size=5000)
+    e = np.linspace(-2.5, 2.5, 11)
+    h = O.sample_histogram(v, e, 1)
+    assert h.sum() == 5000
+    ref, _ = np.histogram(v.real, bins=e)
+    # numpy's bins are half-open except the last one, which is closed
+    assert list(h[1:-2]) == list(ref[:-1]) and h[-2] <= ref[-1]
+
+
+@pytest.mark.parametrize("name,old,new", [("edge goes to the lower bin", "e <= v", "e < v"),
+                                          ("|z|^2 without Im", "re * re + im * im if kind == 0", "re * re if kind == 0")])
+def test_planted_histogram_mistake_is_caught(name, old, new):
+    src = inspect.getsource(O.sample_histogram)
+    assert src.count(old) == 1, name
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    f = ns["sample_histogram"]
+    edges = [0.0, 0.25, 1.0, 4.0]
+    z = np.array([0.5, -0.5, 0.25, 0.0, 3 + 4j, 0.5j, -2.0, 1.0, np.nan, 2j])
+    ok = (list(f(z, edges, 0)) == [0, 2, 3, 1, 3] and list(f(z, edges, 1)) == [2, 3, 2, 2, 0])
+    assert not ok, f"planted mistake '{name}' passed the pins"
