@@ -20,6 +20,8 @@
 // double implementation of the same formulas takes the same decisions.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "permx.h"
 
@@ -269,9 +271,14 @@ extern "C" int perm_sample_histogram(int field, const void* values, int64_t coun
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PERMX_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * (size_t)(nedges + 1), s));
     if (count == 0) return PERMX_OK;
+    // copy from a pageable host buffer of our own: the runtime stages such a
+    // copy before returning, so the caller may reuse `edges` at once even when
+    // it lives in pinned memory
+    const std::vector<double> host_edges(edges, edges + nedges);
     void* d_edges = nullptr;
     PERMX_CUDA(ws_alloc(&d_edges, sizeof(double) * (size_t)nedges, s));
-    cudaError_t e = cudaMemcpyAsync(d_edges, edges, sizeof(double) * (size_t)nedges, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(d_edges, host_edges.data(), sizeof(double) * (size_t)nedges,
+                                    cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         const size_t shmem = sizeof(double) * (size_t)nedges + sizeof(unsigned int) * (size_t)(nedges + 1);
         if (shmem > 48 * 1024) e = cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
