@@ -101,16 +101,16 @@ int fp_arith() { return g_fp_arith.load(); }
 int set_fp_arith(int mode) { return g_fp_arith.exchange(mode); }
 
 int sm_count() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];   // zero-initialised (static storage)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (cached[dev] == 0) {
-        int v = 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
-        cached[dev] = v;
+        cached[dev].store(v, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return v;
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 
 #include "permx.h"
@@ -142,6 +144,19 @@ inline int group_log2(int log2_chunks, int per_warp) {
 int fp_arith();
 
 constexpr int kRyserThreads = 256;
+
+// Resident blocks per SM of a walk kernel at kRyserThreads threads, queried
+// once per kernel.  The cache is atomic because the server's worker thread
+// and the caller's threads may make the first call at the same time.
+template <typename K>
+int occupancy_blocks(std::atomic<int>& slot, K kernel) {
+    int b = slot.load(std::memory_order_relaxed);
+    if (b > 0) return b;
+    b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kRyserThreads, 0) != cudaSuccess || b < 1) b = 1;
+    slot.store(b, std::memory_order_relaxed);
+    return b;
+}
 
 int sm_count();
 cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);   // library memory pool, stream-ordered

@@ -221,25 +221,13 @@ cudaError_t launch_c128(const FpLaunch& L, int grid, cudaStream_t s) {
 }
 template <int N>
 int blocks_per_sm_f64() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_f64_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
-        cached = b;
-    }
-    return cached;
+    static std::atomic<int> slot{0};
+    return occupancy_blocks(slot, ryser_f64_kernel<N>);
 }
 template <int N>
 int blocks_per_sm_c128() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_c128_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
-        cached = b;
-    }
-    return cached;
+    static std::atomic<int> slot{0};
+    return occupancy_blocks(slot, ryser_c128_kernel<N>);
 }
 
 }  // namespace permx

@@ -233,14 +233,8 @@ cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s) {
 
 template <int N>
 int blocks_per_sm_modp() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_modp_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
-        cached = b;
-    }
-    return cached;
+    static std::atomic<int> slot{0};
+    return occupancy_blocks(slot, ryser_modp_kernel<N>);
 }
 
 }  // namespace permx

@@ -372,29 +372,14 @@ cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s) {
 }
 template <int N>
 int blocks_per_sm_x64r() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64r_kernel<N>, kRyserThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
-        cached = b;
-    }
-    return cached;
+    static std::atomic<int> slot{0};
+    return occupancy_blocks(slot, ryser_x64r_kernel<N>);
 }
 template <int N>
 int blocks_per_sm_x64c() {
-    static int cached = -1;
-    if (cached < 0) {
-        int b = 0;
-        cudaError_t e;
-        if constexpr (x64c_paired(N))
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c2_kernel<N>, kRyserThreads, 0);
-        else
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ryser_x64c_kernel<N>, kRyserThreads, 0);
-        if (e != cudaSuccess || b < 1) b = 1;
-        cached = b;
-    }
-    return cached;
+    static std::atomic<int> slot{0};
+    if constexpr (x64c_paired(N)) return occupancy_blocks(slot, ryser_x64c2_kernel<N>);
+    else return occupancy_blocks(slot, ryser_x64c_kernel<N>);
 }
 
 }  // namespace permx
