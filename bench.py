@@ -154,11 +154,25 @@ def cpu_baseline(primes, mats, target_s: float = 16.0):
     O.ryser_modp_gray_range(A, p, k0, k0 + span1)
     dt1 = time.perf_counter() - t1
     O.set_num_threads(cores)
+    # the paper's own CPU algorithm (incremental Gray walk, one thread), the
+    # comparator for its GPU-over-single-threaded-CPU speed-ups: about 4 s
+    from oracle import cpu_walk as W
+    W.modp_gray_range(A, p, k0, k0 + (1 << 16))
+    t2 = time.perf_counter()
+    W.modp_gray_range(A, p, k0, k0 + (1 << 18))
+    rate_w = (1 << 18) / max(time.perf_counter() - t2, 1e-9)
+    span_w = int(min(max(rate_w * 4.0, 1 << 18), 1 << 30))
+    t2 = time.perf_counter()
+    W.modp_gray_range(A, p, k0, k0 + span_w)
+    dt2 = time.perf_counter() - t2
     return {"value": N * span / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"Gray indices [{k0}, {k0 + span}) of S_33 mod {p} (one of 5 primes), "
                       f"{span} subsets x {N} rows, {dt:.1f} s",
             "single_core": {"value": N * span1 / dt1, "unit": UNIT, "cores": 1,
-                            "sample": f"Gray indices [{k0}, {k0 + span1}), {dt1:.1f} s"}}
+                            "sample": f"Gray indices [{k0}, {k0 + span1}), {dt1:.1f} s"},
+            "gray_walk_single_core": {"value": N * span_w / dt2, "unit": UNIT, "cores": 1,
+                                      "kind": "plain CPU Gray-code walk (incremental row sums, uint64 %)",
+                                      "sample": f"Gray indices [{k0}, {k0 + span_w}), {dt2:.1f} s"}}
 
 
 def run_reference(args, rank, world):

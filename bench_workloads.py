@@ -324,6 +324,12 @@ def haar14_plain(args):
     got = out.cpu().numpy()
     worst = max(abs(got[i] - O.perm_dp(mats[i])) / abs(O.perm_dp(mats[i])) for i in range(0, 256, 32))
     terms = 256 * 14 * 2.0 ** 14
+    # the paper's CPU algorithm on one core (plain double Gray walk) over the same 256 matrices
+    from oracle import cpu_walk as W
+    t_w = time.perf_counter()
+    for i in range(256):
+        W.perm(mats[i])
+    walk_s = time.perf_counter() - t_w
     line = {"workload": "haar14_plain", "metric": "perms_per_s", "value": 256 / (res["plain"] / 1e3),
             "unit": "perm/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["plain"], "batched_perms_per_s": 256 / (res["batched"] / 1e3),
@@ -332,6 +338,10 @@ def haar14_plain(args):
             "plain_graph_perms_per_s": 256 / (res["plain_graph"] / 1e3), "plain_graph_ms": res["plain_graph"],
             "kernels_per_call": 4, "graph_launches_plain_graph": 256,
             "max_rel_err_vs_oracle_sample": worst, "dtype": "c128",
+            "cpu_gray_walk_single_core": {"value": 256 / walk_s, "unit": "perm/s", "cores": 1,
+                                          "nominal_terms_per_s": terms / walk_s,
+                                          "kind": "plain CPU Gray-code walk (uncompensated complex double)",
+                                          "sample": f"the same 256 matrices, {walk_s:.2f} s"},
             "config": {"n": 14, "count": 256, "ensemble": "haar_u", "seed": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -420,6 +430,21 @@ def ensembles_batched(args):
             worst_rel = max(worst_rel, err / abs(ref))
             checked += 1
     oracle_rate = oracle_terms / max(oracle_s, 1e-9)
+    # the paper's CPU algorithm on one core (plain double Gray walk): one matrix
+    # of each field at every size, extrapolated to the step by n 2^n terms
+    from oracle import cpu_walk as W
+    walk_terms, walk_s = 0.0, 0.0
+    for cplx, (flat, ns, offs, out) in fields.items():
+        host = flat.cpu().numpy()
+        for g in range(len(ns) // count):
+            i = g * count
+            n = int(ns[i])
+            A = host[offs[i]:offs[i] + n * n].reshape(n, n)
+            t_w = time.perf_counter()
+            W.perm(A)
+            walk_s += time.perf_counter() - t_w
+            walk_terms += n * 2.0 ** n
+    walk_rate = walk_terms / max(walk_s, 1e-9)
     line = {"workload": "ensembles_batched", "metric": "perms_per_s", "value": total_perms / t, "unit": "perm/s",
             "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "nominal_terms_per_s": total_terms / t, "perms_per_step": total_perms,
@@ -429,7 +454,12 @@ def ensembles_batched(args):
             "cpu_baseline": {"value": oracle_rate, "unit": "terms/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"Ryser in double-double on the {checked} checked matrices (n <= 16), "
                                        "n 2^n terms each",
-                             "extrapolated_s_per_step": total_terms / oracle_rate},
+                             "extrapolated_s_per_step": total_terms / oracle_rate,
+                             "gray_walk_single_core": {
+                                 "value": walk_rate, "unit": "terms/s", "cores": 1,
+                                 "kind": "plain CPU Gray-code walk (uncompensated double / complex double)",
+                                 "sample": f"the first matrix of every (ensemble, n) group, {walk_s:.1f} s",
+                                 "extrapolated_s_per_step": total_terms / walk_rate}},
             "dtype": "c128+f64",
             "data": "synthetic, generated on the device (seeded torch generators)",
             "config": {"sizes": list(SIZES), "per_size_and_ensemble": count, "scale_of_50000": args.scale,

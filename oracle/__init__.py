@@ -23,6 +23,9 @@ What it computes, and where the paper defines it:
   ``c_m = #{sigma : sum_i i*sigma(i) = m (mod n)}`` reduced modulo the
   cyclotomic polynomial ``Phi_n`` (definition of ``S_n``, paper §1).
 
+* ``cpu_walk`` — the paper's Gray-code walk as a plain single-threaded CPU
+  program (incremental row sums), the comparator for GPU-over-one-core
+  speed-ups; pinned to the recomputing Ryser above.
 * ``sample_histogram`` — counts of |z|^2, Re z or Im z between given edges
   (the distributions behind the paper's Q-Q plots and tail probabilities).
 * ``sample_stats`` — the sample moments, counts and extremes the paper
@@ -53,12 +56,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, OpenMP)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, OpenMP), and the
+    single-core CPU walks of ``cpu_walk.c`` beside it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-Wall", "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
+    from . import cpu_walk
+    cpu_walk.build(force)
     return _LIB
 
 
