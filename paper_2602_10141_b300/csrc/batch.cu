@@ -237,7 +237,12 @@ __device__ __forceinline__ void dd_pair_add(double& s, double& c, double s2, dou
 }
 
 // One block (kFinalThreads threads) per matrix; thread t folds partials
-// t, t + kFinalThreads, ... in order, then a fixed binary tree.
+// t, t + kFinalThreads, ... in order, then a fixed binary tree (level h adds
+// thread t + h into thread t).  Threads at or past the partial count hold the
+// pair (0, 0), and adding it leaves a pair unchanged, so the tree starts at
+// the first level whose upper half holds partials; its last five levels run
+// in warp 0 with shuffles.  FP64 is slow on B300, so the levels a lone small
+// matrix skips are most of this kernel's time.
 constexpr int kFinalThreads = 128;
 __global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double* __restrict__ partial,
                                                                     const FpFinal* __restrict__ f,
@@ -253,25 +258,41 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double
     }
     sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = c0; sh[2][threadIdx.x] = s1; sh[3][threadIdx.x] = c1;
     __syncthreads();
-    for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+    const int live = x.count < kFinalThreads ? (int)x.count : kFinalThreads;
+    int h = kFinalThreads / 2;
+    while (h > 0 && h >= live) h >>= 1;       // levels that would add only (0, 0) pairs
+    for (; h >= 32; h >>= 1) {
         if (threadIdx.x < h) {
             double a = sh[0][threadIdx.x], ac = sh[1][threadIdx.x];
             dd_pair_add(a, ac, sh[0][threadIdx.x + h], sh[1][threadIdx.x + h]);
             sh[0][threadIdx.x] = a; sh[1][threadIdx.x] = ac;
-            double b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
-            dd_pair_add(b, bc, sh[2][threadIdx.x + h], sh[3][threadIdx.x + h]);
-            sh[2][threadIdx.x] = b; sh[3][threadIdx.x] = bc;
+            if (cplx) {
+                double b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
+                dd_pair_add(b, bc, sh[2][threadIdx.x + h], sh[3][threadIdx.x + h]);
+                sh[2][threadIdx.x] = b; sh[3][threadIdx.x] = bc;
+            }
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double sg = (x.negate ? -1.0 : 1.0) * (x.twice ? 2.0 : 1.0);
-        const double re = sg * (sh[0][0] + sh[1][0]);
-        if (cplx) {
-            const double im = sg * (sh[2][0] + sh[3][0]);
-            reinterpret_cast<double2*>(out)[x.out_index] = make_double2(re, im);
-        } else {
-            reinterpret_cast<double*>(out)[x.out_index] = re;
+    if (threadIdx.x < 32) {
+        double a = sh[0][threadIdx.x], ac = sh[1][threadIdx.x], b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
+        for (; h > 0; h >>= 1) {
+            const double a2 = __shfl_down_sync(0xffffffffu, a, h), ac2 = __shfl_down_sync(0xffffffffu, ac, h);
+            const double b2 = __shfl_down_sync(0xffffffffu, b, h), bc2 = __shfl_down_sync(0xffffffffu, bc, h);
+            if (threadIdx.x < h) {
+                dd_pair_add(a, ac, a2, ac2);
+                if (cplx) dd_pair_add(b, bc, b2, bc2);
+            }
+        }
+        if (threadIdx.x == 0) {
+            const double sg = (x.negate ? -1.0 : 1.0) * (x.twice ? 2.0 : 1.0);
+            const double re = sg * (a + ac);
+            if (cplx) {
+                const double im = sg * (b + bc);
+                reinterpret_cast<double2*>(out)[x.out_index] = make_double2(re, im);
+            } else {
+                reinterpret_cast<double*>(out)[x.out_index] = re;
+            }
         }
     }
 }
