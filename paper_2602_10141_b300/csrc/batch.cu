@@ -121,46 +121,64 @@ int sm_count() {
 // sigma_i = 60 - floor(log2(sum_j |a_ij|)) (complex: |re| + |im|), entries
 // A_ij = 2 round(a_ij 2^(sigma_i - 1)) (even, so halves are exact), the
 // Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij)/2, zero padding, and
-// one trailing word with -sum_i sigma_i.  W = int64 words per entry.
+// one trailing word with -sum_i sigma_i.  W = int64 words per entry.  The
+// matrix is read once into shared memory; the row scales take one thread per
+// row (the float sum in column order), the conversions one thread per entry.
+constexpr int kStageX64Threads = 128;
 template <int W>
-__global__ void stage_x64_kernel(const double* __restrict__ A, const StageDesc* __restrict__ d,
-                                 int64_t* __restrict__ colT) {
+__global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const double* __restrict__ A,
+                                                                   const StageDesc* __restrict__ d,
+                                                                   int64_t* __restrict__ colT) {
+    // the matrix, row-major: the float entries, each replaced in place by its
+    // integer A_ij once the row scales are known
+    __shared__ long long buf[PERMX_MAX_N_FP * PERMX_MAX_N_FP * W];
+    __shared__ int sig_row[PERMX_MAX_N_FP];   // sigma_i, or kNonFinite
     __shared__ int sig_sum, bad;
+    constexpr int kNonFinite = -1 << 30;
     const StageDesc s = d[blockIdx.x];
-    const int n = s.n, ld = s.ld;
+    const int n = s.n, ld = s.ld, nw = n * W, tot = n * nw;
     int64_t* base = colT + s.dst * W;   // dst counts entries of W words
+    const long long* src = reinterpret_cast<const long long*>(A + s.src * W);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) buf[e] = src[e];   // one coalesced pass
     if (threadIdx.x == 0) {
         sig_sum = 0;
         bad = 0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
-        if (i >= n) {
-            for (int j = 0; j <= n; ++j)
-                for (int w = 0; w < W; ++w) base[((int64_t)j * ld + i) * W + w] = 0;
-            continue;
-        }
-        const double* row = A + (s.src + (int64_t)i * n) * W;
+    // the row scale from sum_j |a_ij|, summed in column order by one thread per row
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double S = 0.0;
-        for (int j = 0; j < n * W; ++j) S += fabs(row[j]);
+        for (int j = 0; j < nw; ++j) S += fabs(__longlong_as_double(buf[i * nw + j]));
         // a NaN or infinite entry makes S non-finite: the matrix is flagged (its
-        // permanent is reported as NaN) and staged as zeros
+        // permanent is reported as NaN) and the row staged as zeros
         const bool finite = isfinite(S);
         if (!finite) atomicOr(&bad, 1);
         const int sig = finite && S > 0.0 ? 60 - ilogb(S) : 0;
-        int64_t sum[W];
-        for (int w = 0; w < W; ++w) sum[w] = 0;
-        for (int j = 0; j < n; ++j)
-            for (int w = 0; w < W; ++w) {
-                const int64_t a = finite ? 2 * (int64_t)llrint(ldexp(row[j * W + w], sig - 1)) : 0;
-                base[((int64_t)j * ld + i) * W + w] = a;
-                sum[w] += a;
-            }
-        for (int w = 0; w < W; ++w)
-            base[((int64_t)n * ld + i) * W + w] = base[((int64_t)(n - 1) * ld + i) * W + w] - sum[w] / 2;
+        sig_row[i] = finite ? sig : kNonFinite;
         atomicAdd(&sig_sum, sig);
     }
     __syncthreads();
+    // entries, one thread each: A_ij = 2 round(a_ij 2^(sigma_i - 1))
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int i = e / nw, jw = e - i * nw, j = jw / W, w = jw - j * W;
+        const int sig = sig_row[i];
+        const int64_t a = sig != kNonFinite ? 2 * (int64_t)llrint(ldexp(__longlong_as_double(buf[e]), sig - 1)) : 0;
+        buf[e] = a;
+        base[((int64_t)j * ld + i) * W + w] = a;
+    }
+    // padding rows n..ld-1 of every column, the x column included
+    for (int e = threadIdx.x; e < (ld - n) * (n + 1) * W; e += blockDim.x) {
+        const int q = e / W, w = e - q * W, j = q / (ld - n), i = n + (q - j * (ld - n));
+        base[((int64_t)j * ld + i) * W + w] = 0;
+    }
+    __syncthreads();
+    // the Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij) / 2, exact (entries are even)
+    for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
+        const int i = e / W, w = e - i * W;
+        int64_t sum = 0;
+        for (int j = 0; j < n; ++j) sum += buf[i * nw + j * W + w];
+        base[((int64_t)n * ld + i) * W + w] = buf[i * nw + (n - 1) * W + w] - sum / 2;
+    }
     if (threadIdx.x == 0) {
         base[(int64_t)(n + 1) * ld * W] = -(int64_t)sig_sum;
         base[(int64_t)(n + 1) * ld * W + 1] = bad;   // 1: non-finite entry, result NaN
@@ -326,10 +344,10 @@ cudaError_t launch_stage_x64(bool cplx, const void* A, const StageDesc* d, int64
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (cplx)
-        stage_x64_kernel<2><<<(unsigned)count, 64, 0, s>>>(static_cast<const double*>(A), d,
+        stage_x64_kernel<2><<<(unsigned)count, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), d,
                                                             static_cast<int64_t*>(colT));
     else
-        stage_x64_kernel<1><<<(unsigned)count, 64, 0, s>>>(static_cast<const double*>(A), d,
+        stage_x64_kernel<1><<<(unsigned)count, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), d,
                                                             static_cast<int64_t*>(colT));
     return cudaGetLastError();
 }
