@@ -209,6 +209,17 @@ int perm_plan_destroy(perm_plan* plan);
 int perm_tune_set(int field, int32_t n, int32_t ell);
 int perm_tune_get(int field, int32_t n);
 int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* best_ell);
+/* Persist the tuning table (host only, no GPU work).  perm_tune_save writes
+ * every pinned (field, n, ell) to the text file `path` ("permx-tune 1", then
+ * one "field n ell" line per entry) through a temporary file renamed into
+ * place; perm_tune_load reads such a file, checks every entry against the
+ * perm_tune_set limits and, only if all pass, replaces the whole table
+ * (entries absent from the file return to the built-in rule).  Errors:
+ * EINVAL (NULL or empty path, malformed, out-of-range or repeated entry,
+ * missing header; the table is left unchanged), EIO (the file cannot be
+ * opened, read or written). */
+int perm_tune_save(const char* path);
+int perm_tune_load(const char* path);
 
 /* ------------------------------------------------------------------------
  * Exact perm(S_n) of the Schur matrix S_n = (exp(2 pi i jk/n))_{j,k<n}

@@ -74,6 +74,8 @@ def _load() -> ctypes.CDLL:
         "perm_tune_set": ([ctypes.c_int, i32, i32], ctypes.c_int),
         "perm_tune_get": ([ctypes.c_int, i32], ctypes.c_int),
         "perm_autotune": ([ctypes.c_int, i32, i64, i32, P(i32)], ctypes.c_int),
+        "perm_tune_save": ([ctypes.c_char_p], ctypes.c_int),
+        "perm_tune_load": ([ctypes.c_char_p], ctypes.c_int),
         "permx_get_fp_arith": ([], ctypes.c_int),
         "perm_c128_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
         "perm_f64_gather": ([vp, i32, i64, P(i32), P(i32), i32, i64, vp, vp], ctypes.c_int),
@@ -277,6 +279,23 @@ def perm_tune_set(field: int, n: int, ell: int) -> None:
 
 def perm_tune_get(field: int, n: int) -> int:
     return _check(_lib.perm_tune_get(field, n))
+
+
+def _tune_path(path) -> bytes:
+    path = path if path is not None else os.environ.get("PERMX_TUNE_CACHE")
+    if not path:
+        raise ValueError("no tuning-file path given and PERMX_TUNE_CACHE is not set")
+    return os.fsencode(path)
+
+
+def perm_tune_save(path=None) -> None:
+    """Write the pinned chunk lengths to ``path`` (default: $PERMX_TUNE_CACHE)."""
+    _check(_lib.perm_tune_save(_tune_path(path)))
+
+
+def perm_tune_load(path=None) -> None:
+    """Replace the tuning table by the file at ``path`` (default: $PERMX_TUNE_CACHE)."""
+    _check(_lib.perm_tune_load(_tune_path(path)))
 
 
 def perm_autotune(field: int, n: int, batch: int, reps: int = 3) -> int:

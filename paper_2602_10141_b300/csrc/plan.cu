@@ -9,7 +9,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "batch.h"
@@ -166,6 +168,70 @@ int perm_tune_get(int field, int32_t n) {
     if (n < 1 || n > PERMX_MAX_N_MODP) return fail(PERMX_EINVAL, "bad n");
     const int bits = walk_bits(n, 1);
     return chunk_log2((Field)field, n, bits);
+}
+
+// Tuning-table persistence.  The file is text: a header line "permx-tune 1",
+// then one line "field n ell" per pinned entry.  Saving writes a temporary
+// file and renames it over `path`, so a reader never sees half a table;
+// loading checks every line against the perm_tune_set limits before it
+// changes anything, then replaces the whole table.
+int perm_tune_save(const char* path) {
+    clear_error();
+    if (!path || !*path) return fail(PERMX_EINVAL, "NULL or empty path");
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return fail(PERMX_EIO, "cannot open the tuning file for writing");
+    bool ok = std::fprintf(f, "permx-tune 1\n") > 0;
+    for (int field = 0; field < 3 && ok; ++field)
+        for (int n = 1; n <= PERMX_MAX_N_MODP && ok; ++n) {
+            const int t = tune_get(field, n);
+            if (t > 0) ok = std::fprintf(f, "%d %d %d\n", field, n, t) > 0;
+        }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(PERMX_EIO, "cannot write the tuning file");
+    }
+    return PERMX_OK;
+}
+
+int perm_tune_load(const char* path) {
+    clear_error();
+    if (!path || !*path) return fail(PERMX_EINVAL, "NULL or empty path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(PERMX_EIO, "cannot open the tuning file");
+    int table[3][PERMX_MAX_N_MODP + 1] = {};
+    char line[256];
+    int rc = PERMX_OK, lineno = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        ++lineno;
+        if (!std::strchr(line, '\n') && !std::feof(f)) {
+            rc = fail(PERMX_EINVAL, "tuning file: line too long");
+            break;
+        }
+        if (lineno == 1) {
+            if (std::strcmp(line, "permx-tune 1\n") != 0 && std::strcmp(line, "permx-tune 1") != 0) {
+                rc = fail(PERMX_EINVAL, "tuning file: missing 'permx-tune 1' header");
+                break;
+            }
+            continue;
+        }
+        int field = -1, n = 0, ell = -1, used = 0;
+        if (std::sscanf(line, "%d %d %d %n", &field, &n, &ell, &used) != 3 || line[used] != '\0' ||
+            field < 0 || field > 2 || n < 1 || n > PERMX_MAX_N_MODP || ell < 1 ||
+            ell > (field == PERMX_FIELD_MODP ? PERMX_MAX_ELL_MODP : PERMX_MAX_ELL_FP) || table[field][n]) {
+            rc = fail(PERMX_EINVAL, "tuning file: bad or repeated entry on line " + std::to_string(lineno));
+            break;
+        }
+        table[field][n] = ell;
+    }
+    if (rc == PERMX_OK && lineno == 0) rc = fail(PERMX_EINVAL, "tuning file: empty");
+    if (rc == PERMX_OK && std::ferror(f)) rc = fail(PERMX_EIO, "cannot read the tuning file");
+    std::fclose(f);
+    if (rc) return rc;
+    for (int field = 0; field < 3; ++field)
+        for (int n = 1; n <= PERMX_MAX_N_MODP; ++n) tune_set(field, n, table[field][n]);
+    return PERMX_OK;
 }
 
 int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* best_ell) {

@@ -129,3 +129,57 @@ def test_schur_crt_primes_argument_checks(px):
         with pytest.raises(px.PermxError):
             px.perm_schur_crt_primes(n, bad)
         assert what in px.last_error(), (bad, px.last_error())
+
+
+def test_tuning_table_save_and_load(px, tmp_path, monkeypatch):
+    """perm_tune_save / perm_tune_load round-trip the pinned entries, replace
+    the whole table, reject malformed files without touching the table, and
+    take $PERMX_TUNE_CACHE as the default path."""
+    f = tmp_path / "tune.txt"
+    d_c = px.perm_tune_get(px.FIELD_C128, 20)
+    d_m = px.perm_tune_get(px.FIELD_MODP, 40)
+    d_r = px.perm_tune_get(px.FIELD_F64, 9)
+    try:
+        px.perm_tune_set(px.FIELD_C128, 20, 7)
+        px.perm_tune_set(px.FIELD_MODP, 40, 25)
+        px.perm_tune_save(str(f))
+        lines = f.read_text().splitlines()
+        assert lines[0] == "permx-tune 1"
+        assert sorted(lines[1:]) == sorted([f"{px.FIELD_C128} 20 7", f"{px.FIELD_MODP} 40 25"])
+        assert not (tmp_path / "tune.txt.tmp").exists()
+        # loading replaces the table: entries not in the file return to the rule
+        px.perm_tune_set(px.FIELD_C128, 20, 0)
+        px.perm_tune_set(px.FIELD_MODP, 40, 0)
+        px.perm_tune_set(px.FIELD_F64, 9, 5)
+        px.perm_tune_load(str(f))
+        assert px.perm_tune_get(px.FIELD_C128, 20) == 7
+        assert px.perm_tune_get(px.FIELD_MODP, 40) == 25
+        assert px.perm_tune_get(px.FIELD_F64, 9) == d_r
+        # malformed files change nothing
+        for text in ("", "permx-tune 2\n", "permx-tune 1\n0 20 17\n", "permx-tune 1\n2 40 31\n",
+                     "permx-tune 1\n0 49 5\n", "permx-tune 1\n3 10 3\n", "permx-tune 1\n0 20 7\n0 20 8\n",
+                     "permx-tune 1\n0 20 7 9\n", "permx-tune 1\n0 20\n", "permx-tune 1\n0 20 0\n"):
+            bad = tmp_path / "bad.txt"
+            bad.write_text(text)
+            with pytest.raises(px.PermxError):
+                px.perm_tune_load(str(bad))
+            assert px.perm_tune_get(px.FIELD_C128, 20) == 7
+        with pytest.raises(px.PermxError):
+            px.perm_tune_load(str(tmp_path / "missing.txt"))
+        with pytest.raises(px.PermxError):
+            px.perm_tune_save(str(tmp_path / "no_such_dir" / "t.txt"))
+        # the environment variable supplies the default path
+        monkeypatch.setenv("PERMX_TUNE_CACHE", str(tmp_path / "env.txt"))
+        px.perm_tune_save()
+        px.perm_tune_set(px.FIELD_C128, 20, 0)
+        px.perm_tune_load()
+        assert px.perm_tune_get(px.FIELD_C128, 20) == 7
+        monkeypatch.delenv("PERMX_TUNE_CACHE")
+        with pytest.raises(ValueError):
+            px.perm_tune_save()
+    finally:
+        px.perm_tune_set(px.FIELD_C128, 20, 0)
+        px.perm_tune_set(px.FIELD_MODP, 40, 0)
+        px.perm_tune_set(px.FIELD_F64, 9, 0)
+    assert px.perm_tune_get(px.FIELD_C128, 20) == d_c
+    assert px.perm_tune_get(px.FIELD_MODP, 40) == d_m
