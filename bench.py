@@ -122,6 +122,43 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def device_info(torch, index: int) -> dict:
+    """The GPU and host the numbers were taken on."""
+    prop = torch.cuda.get_device_properties(index)
+    return {"name": prop.name, "sm_count": prop.multi_processor_count,
+            "memory_gib": round(prop.total_memory / 2 ** 30, 1), "host_cores": os.cpu_count()}
+
+
+class _JsonlTee:
+    """Copies every JSON object line written to stdout into a JSONL log, with
+    the time it was written (``--jsonl PATH``)."""
+
+    def __init__(self, stream, path: str):
+        self.stream, self.path, self.buf = stream, path, ""
+
+    def write(self, text: str) -> int:
+        self.buf += text
+        while "\n" in self.buf:
+            line, self.buf = self.buf.split("\n", 1)
+            if line.startswith("{"):
+                try:
+                    rec = json.loads(line)
+                except ValueError:
+                    rec = None
+                if isinstance(rec, dict):
+                    rec.setdefault("logged_at", time.strftime("%Y-%m-%dT%H:%M:%S%z"))
+                    rec.setdefault("argv", sys.argv[1:])
+                    with open(self.path, "a") as f:
+                        f.write(json.dumps(rec) + "\n")
+        return self.stream.write(text)
+
+    def flush(self):
+        self.stream.flush()
+
+    def __getattr__(self, name):
+        return getattr(self.stream, name)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -243,8 +280,12 @@ def main():
                     help="schur_long: stop after this many checkpointed slices per n (0 = run to the end)")
     ap.add_argument("--scale", type=float, default=0.02,
                     help="ensembles_batched / serving: fraction of the full sample counts")
+    ap.add_argument("--jsonl", default="",
+                    help="also append every JSON result line (with a timestamp and the arguments) to this file")
     args = ap.parse_args()
     rank, world, local = _rank_env()
+    if args.jsonl and rank == 0:
+        sys.stdout = _JsonlTee(sys.stdout, args.jsonl)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.profile_case:
@@ -353,6 +394,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
                     "d2h_bytes_per_step": 4 * NPRIMES},
             "gpu_launches": 4 * args.steps,   # metadata, staging, Gray walk, finalize per step
+            "device": device_info(torch, local),
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(primes, mats)

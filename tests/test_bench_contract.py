@@ -9,11 +9,12 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(env_extra):
+def _run(env_extra, extra_args=()):
     env = dict(os.environ)
     env.update(env_extra)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "1"], capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
+                        "--warmup", "1", *extra_args], capture_output=True, text=True, timeout=300, env=env,
+                       cwd=ROOT)
     return r
 
 
@@ -38,3 +39,19 @@ def test_reference_arm_other_ranks_are_silent():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2", "OMP_NUM_THREADS": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_jsonl_log_copies_the_result_line(tmp_path):
+    """--jsonl appends each printed JSON line, stamped with the time and the
+    arguments, and leaves stdout unchanged."""
+    log = tmp_path / "runs.jsonl"
+    for _ in range(2):
+        r = _run({"OMP_NUM_THREADS": "1"}, ("--jsonl", str(log)))
+        assert r.returncode == 0, r.stderr[-2000:]
+    printed = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    logged = [json.loads(ln) for ln in log.read_text().splitlines()]
+    assert len(printed) == 1 and len(logged) == 2
+    for rec in logged:
+        assert rec["impl"] == "reference" and rec["metric"] == printed[0]["metric"]
+        assert rec["logged_at"] and "--jsonl" in rec["argv"]
+    assert "logged_at" not in printed[0]
