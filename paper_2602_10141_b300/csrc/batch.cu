@@ -656,11 +656,11 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
     const double* Ad = static_cast<const double*>(A);
     if (X.x64) {
         if (cplx)
-            stage_x64_kernel<2><<<(unsigned)batch, 64, 0, s>>>(Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage),
-                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+            stage_x64_kernel<2><<<(unsigned)batch, kStageX64Threads, 0, s>>>(
+                Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<int64_t*>(d + X.o_col));
         else
-            stage_x64_kernel<1><<<(unsigned)batch, 64, 0, s>>>(Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage),
-                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+            stage_x64_kernel<1><<<(unsigned)batch, kStageX64Threads, 0, s>>>(
+                Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<int64_t*>(d + X.o_col));
     } else if (cplx) {
         stage_columns_kernel<double2><<<(unsigned)batch, 256, 0, s>>>(
             reinterpret_cast<const double2*>(Ad), reinterpret_cast<const StageDesc*>(d + X.o_stage),
