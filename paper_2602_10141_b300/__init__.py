@@ -135,19 +135,67 @@ def version() -> str:
 
 
 # ---------------------------------------------------------------------------
+# tensor checks: the C-ABI takes bare device pointers and cannot see sizes or
+# dtypes, so the binding rejects a tensor that would make a kernel read or
+# write outside it before the pointer reaches the library
+# ---------------------------------------------------------------------------
+
+def _need(n: np.ndarray, offset: np.ndarray, max_n: int) -> int:
+    """Elements a batch reads: max over b of offset[b] + n[b]^2, over the sizes
+    the library accepts (it rejects the others itself, with PERMX_EINVAL)."""
+    if len(n) != len(offset):
+        raise ValueError(f"n has {len(n)} entries, offset {len(offset)}")
+    ok = (n >= 1) & (n <= max_n)
+    if not ok.any():
+        return 0
+    return int(np.max(offset[ok].astype(np.int64) + n[ok].astype(np.int64) ** 2))
+
+
+def _dtypes(kind: str):
+    import torch
+    if kind == "c128":
+        return (torch.complex128,)
+    if kind == "f64":
+        return (torch.float64,)
+    return tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
+
+
+def _tensors(*specs) -> None:
+    """specs: (tensor, name, kind, elements needed).  Type, dtype, layout and
+    size of every tensor first, then that all of them are on a CUDA device."""
+    import torch
+    for t, what, kind, need in specs:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{what} must be a torch tensor")
+        dts = _dtypes(kind)
+        if t.dtype not in dts:
+            raise TypeError(f"{what} must be {' or '.join(str(d) for d in dts)}, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{what} holds {t.numel()} elements; the call needs {need}")
+    for t, what, _, _ in specs:
+        if not t.is_cuda:
+            raise ValueError(f"{what} must be on a CUDA device")
+
+
+# ---------------------------------------------------------------------------
 # batched device calls (arguments: device tensors + host index arrays)
 # ---------------------------------------------------------------------------
 
 def perm_c128(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
     """out[b] = perm of the n[b] x n[b] complex128 matrix at A.view(-1)[offset[b]:]."""
     n, offset = _i32(n), _i64(offset)
+    _tensors((A, "A", "c128", _need(n, offset, MAX_N_FP)), (out, "out", "c128", len(n)))
     _check(_lib.perm_c128(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
                           out.data_ptr(), _stream(stream)))
     return out
 
 
 def perm_f64(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
+    """out[b] = perm of the n[b] x n[b] float64 matrix at A.view(-1)[offset[b]:]."""
     n, offset = _i32(n), _i64(offset)
+    _tensors((A, "A", "f64", _need(n, offset, MAX_N_FP)), (out, "out", "f64", len(n)))
     _check(_lib.perm_f64(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
                          out.data_ptr(), _stream(stream)))
     return out
@@ -156,6 +204,7 @@ def perm_f64(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
 def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out, stream=None):
     """A: device int32/uint32 residues (< p[b]); out: device int32 tensor of residues."""
     n, offset, p = _i32(n), _i64(offset), _u32(p)
+    _tensors((A, "A", "modp", _need(n, offset, MAX_N_MODP)), (out, "out", "modp", len(n)))
     _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                           _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
     return out
@@ -173,6 +222,9 @@ def perm_gather(U, rows, cols, out, stream=None):
     f = _lib.perm_c128_gather if U.dtype == torch.complex128 else _lib.perm_f64_gather
     if U.dtype not in (torch.complex128, torch.float64):
         raise TypeError("U must be complex128 or float64")
+    _tensors((out, "out", "c128" if U.dtype == torch.complex128 else "f64", rows.shape[0]))
+    if not U.is_cuda:
+        raise ValueError("U must be on a CUDA device")
     _check(f(U.data_ptr(), U.shape[0], U.stride(0), _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
              rows.shape[1], rows.shape[0], out.data_ptr(), _stream(stream)))
     return out
@@ -181,16 +233,29 @@ def perm_gather(U, rows, cols, out, stream=None):
 HIST_ABS2, HIST_RE, HIST_IM = 0, 1, 2
 
 
-def perm_sample_histogram(values, edges, kind: int = 0, stream=None):
-    """Counts of |z|^2 (kind 0), Re z (1) or Im z (2) over sorted host `edges`:
-    a numpy int64 array of len(edges) + 1 (below, bins, at-or-above).  Synchronises."""
+def _values_field(values) -> int:
+    """Field code of a device tensor of permanents (complex128 or float64)."""
     import torch
+    if not isinstance(values, torch.Tensor):
+        raise TypeError("values must be a torch tensor")
     if values.dtype == torch.complex128:
         field = FIELD_C128
     elif values.dtype == torch.float64:
         field = FIELD_F64
     else:
         raise TypeError("values must be complex128 or float64")
+    if not values.is_contiguous():
+        raise ValueError("values must be contiguous")
+    if not values.is_cuda:
+        raise ValueError("values must be on a CUDA device")
+    return field
+
+
+def perm_sample_histogram(values, edges, kind: int = 0, stream=None):
+    """Counts of |z|^2 (kind 0), Re z (1) or Im z (2) over sorted host `edges`:
+    a numpy int64 array of len(edges) + 1 (below, bins, at-or-above).  Synchronises."""
+    import torch
+    field = _values_field(values)
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
     counts = torch.empty(len(e) + 1, dtype=torch.int64, device=values.device)
     _check(_lib.perm_sample_histogram(field, values.data_ptr(), values.numel(), kind, _p(e, ctypes.c_double),
@@ -214,15 +279,11 @@ class PermStats(ctypes.Structure):
 def perm_sample_stats_async(values, out, threshold: float = float("inf"), real_tol: float = 0.0, stream=None):
     """Enqueue perm_sample_stats on `stream`: values is a device complex128 or
     float64 tensor, out a device uint8 tensor of at least sizeof(perm_stats_t)."""
-    import torch
-    if values.dtype == torch.complex128:
-        field = FIELD_C128
-    elif values.dtype == torch.float64:
-        field = FIELD_F64
-    else:
-        raise TypeError("values must be complex128 or float64")
+    field = _values_field(values)
     if out.numel() * out.element_size() < ctypes.sizeof(PermStats):
         raise ValueError("output buffer too small for perm_stats_t")
+    if not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor")
     _check(_lib.perm_sample_stats(field, values.data_ptr(), values.numel(), threshold, real_tol,
                                   out.data_ptr(), _stream(stream)))
     return out
@@ -247,17 +308,24 @@ class Plan:
         n, offset = _i32(n), _i64(offset)
         pp = _u32(p) if p is not None else None
         self._keep = (n, offset, pp)
+        self._kind = {FIELD_C128: "c128", FIELD_F64: "f64", FIELD_MODP: "modp"}.get(field)
+        self._need = _need(n, offset, MAX_N_MODP if field == FIELD_MODP else MAX_N_FP)
         h = ctypes.c_void_p()
         _check(_lib.perm_plan_create(field, _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                                      _p(pp, ctypes.c_uint32) if pp is not None else None, len(n), _stream(stream),
                                      ctypes.byref(h)))
         self.h = h
 
+    def _args(self, A, out):
+        _tensors((A, "A", self._kind, self._need), (out, "out", self._kind, len(self._keep[0])))
+
     def execute(self, A, out, stream=None):
+        self._args(A, out)
         _check(_lib.perm_plan_execute(self.h, A.data_ptr(), out.data_ptr(), _stream(stream)))
         return out
 
     def graph_launch(self, A, out, stream=None):
+        self._args(A, out)
         _check(_lib.perm_plan_graph_launch(self.h, A.data_ptr(), out.data_ptr(), _stream(stream)))
         return out
 
@@ -308,6 +376,7 @@ def perm_modp_noalloc(A, n: Sequence[int], offset: Sequence[int], p: Sequence[in
     """perm_modp for callers that cannot allocate: at most 64 matrices per call,
     intermediates in the library's fixed device array (see include/permx.h)."""
     n, offset, p = _i32(n), _i64(offset), _u32(p)
+    _tensors((A, "A", "modp", _need(n, offset, MAX_N_MODP)), (out, "out", "modp", len(n)))
     _check(_lib.perm_modp_noalloc(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
                                   _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
     return out
@@ -346,6 +415,7 @@ def perm_modp_host(A: np.ndarray, n, offset, p, out: np.ndarray | None = None, s
 
 def perm_modp_gray_range(A, n: int, p: int, k0: int, k1: int, stream=None) -> int:
     """Signed Ryser sum over Gray indices [k0, k1) of one device matrix, mod p (no (-1)^n)."""
+    _tensors((A, "A", "modp", int(n) * int(n) if 1 <= n <= MAX_N_MODP else 0))
     r = ctypes.c_uint32(0)
     _check(_lib.perm_modp_gray_range(A.data_ptr(), n, p, k0, k1, ctypes.byref(r), _stream(stream)))
     return int(r.value)

@@ -183,3 +183,47 @@ def test_tuning_table_save_and_load(px, tmp_path, monkeypatch):
         px.perm_tune_set(px.FIELD_F64, 9, 0)
     assert px.perm_tune_get(px.FIELD_C128, 20) == d_c
     assert px.perm_tune_get(px.FIELD_MODP, 40) == d_m
+
+
+def test_binding_rejects_tensors_that_do_not_fit(px):
+    """The binding checks dtype, contiguity, size (against n and offset) and
+    device before a pointer reaches the library, whose C-ABI cannot see them."""
+    import torch
+    n, off = [3, 4], [0, 9]                      # needs 9 + 16 = 25 elements
+    c = torch.zeros(25, dtype=torch.complex128)  # CPU tensors: every check before the device one
+    out_c = torch.zeros(2, dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        px.perm_c128(c.real.contiguous(), n, off, out_c)            # float64 where complex128 is due
+    with pytest.raises(ValueError, match="needs 25"):
+        px.perm_c128(c[:24], n, off, out_c)
+    with pytest.raises(ValueError, match="contiguous"):
+        px.perm_c128(torch.zeros(50, dtype=torch.complex128)[::2], n, off, out_c)
+    with pytest.raises(ValueError, match="needs 2"):
+        px.perm_c128(c, n, off, out_c[:1])
+    with pytest.raises(ValueError, match="entries"):
+        px.perm_c128(c, n, [0], out_c)
+    with pytest.raises(ValueError, match="CUDA"):
+        px.perm_c128(c, n, off, out_c)
+    with pytest.raises(TypeError):
+        px.perm_f64(c, n, off, torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):
+        px.perm_f64(torch.zeros(25, dtype=torch.float64), n, off, torch.zeros(2, dtype=torch.float64))
+    r = torch.zeros(25, dtype=torch.int32)
+    with pytest.raises(ValueError, match="needs 25"):
+        px.perm_modp(r[:20], n, off, [7, 7], torch.zeros(2, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        px.perm_modp(r.to(torch.int64), n, off, [7, 7], torch.zeros(2, dtype=torch.int32))
+    with pytest.raises(ValueError, match="CUDA"):
+        px.perm_modp_noalloc(r, n, off, [7, 7], torch.zeros(2, dtype=torch.int32))
+    with pytest.raises(ValueError, match="needs 36"):
+        px.perm_modp_gray_range(r, 6, 7, 0, 4)
+    with pytest.raises(TypeError):
+        px.perm_c128([0j] * 25, n, off, out_c)                     # not a tensor
+    with pytest.raises(ValueError, match="CUDA"):
+        px.perm_gather(torch.zeros((4, 4), dtype=torch.complex128), [[0, 1]], [[1, 2]], out_c)
+    with pytest.raises(TypeError):
+        px.perm_sample_stats(torch.zeros(4, dtype=torch.float32))
+    with pytest.raises(ValueError, match="CUDA"):
+        px.perm_sample_stats(torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError, match="contiguous"):
+        px.perm_sample_histogram(torch.zeros(8, dtype=torch.complex128)[::2], [0.0, 1.0])
