@@ -8,6 +8,8 @@
 // process resumes at the last finished slice.
 #include <cuda_runtime.h>
 
+#include <unistd.h>
+
 #include <cerrno>
 #include <cstdio>
 #include <cstring>
@@ -117,17 +119,25 @@ int write_checkpoint(const std::string& path, const SchurState& st) {
     const std::string tmp = path + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "wb");
     if (!f) return fail(PERMX_EIO, "cannot open checkpoint " + tmp + ": " + std::strerror(errno));
-    const bool ok = std::fwrite(body.data(), 1, body.size(), f) == body.size() && std::fflush(f) == 0;
-    std::fclose(f);
-    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0)
+    // on disk before the rename makes it the checkpoint, so a crash leaves the
+    // old file or the new one, never a truncated one
+    bool ok = std::fwrite(body.data(), 1, body.size(), f) == body.size() && std::fflush(f) == 0 &&
+              fsync(fileno(f)) == 0;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) {
+        std::remove(tmp.c_str());
         return fail(PERMX_EIO, "cannot write checkpoint " + path);
+    }
     return PERMX_OK;
 }
 
 // 1 = loaded, 0 = no file, <0 = error (corrupt or mismatched)
 int read_checkpoint(const std::string& path, SchurState& st) {
     FILE* f = std::fopen(path.c_str(), "rb");
-    if (!f) return 0;
+    if (!f) {
+        if (errno == ENOENT) return 0;
+        return fail(PERMX_EIO, "cannot read checkpoint " + path + ": " + std::strerror(errno));
+    }
     std::string text;
     char buf[4096];
     size_t got;

@@ -34,3 +34,15 @@ def test_checkpoint_from_other_run_rejected(px, tmp_path):
         px.perm_schur_crt_ex(19, 0, str(ck))
     assert e.value.code == px.PERMX_EINVAL
     assert "different run" in px.last_error()
+
+
+def test_unreadable_checkpoint_path_is_an_error(px, tmp_path):
+    """A checkpoint path that cannot be opened for a reason other than 'no such
+    file' (here a regular file used as a directory) is an I/O error, reported
+    before any GPU work, not a fresh start."""
+    f = tmp_path / "plain_file"
+    f.write_text("x")
+    with pytest.raises(px.PermxError) as e:
+        px.perm_schur_crt_ex(19, 0, str(f / "run.ckpt"))
+    assert e.value.code == px.PERMX_EIO
+    assert "cannot read checkpoint" in px.last_error()
