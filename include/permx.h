@@ -105,9 +105,10 @@ int perm_f64(const double* A, const int32_t* n, const int64_t* offset, int64_t b
 int permx_set_fp_arith(int mode);
 int permx_get_fp_arith(void);
 
-/* F_p permanents (paper §2.1).  A holds residues in [0, p[b]) (entries >= p
- * give unspecified results; the checked host path perm_modp_host rejects
- * them), p host array [batch] of primes 2 < p < 2^31, out device array
+/* F_p permanents (paper §2.1).  A holds residues mod p[b] (uint32; entries
+ * at or above p[b] are taken mod p[b] during staging, so the result is the
+ * permanent of A mod p[b]; the checked host path perm_modp_host rejects
+ * them instead), p host array [batch] of primes 2 < p < 2^31, out device array
  * [batch] of canonical residues in [0, p[b]).  1 <= n[b] <= PERMX_MAX_N_MODP.
  * Exact: the result does not depend on chunking or batch composition, so a
  * call whose matrices would make fewer than 2^18 chunks shortens its chunks

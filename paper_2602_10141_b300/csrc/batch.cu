@@ -215,13 +215,19 @@ __device__ __forceinline__ double2 x_entry(const double2* __restrict__ row, int 
 
 // One block per matrix: colT[dst + j*ld + i] = A[src + i*n + j], padding
 // zeroed, and in the Nijenhuis-Wilf form the x column at colT[dst + n*ld + i].
+// A residue at or above p is taken mod p (the walk's modular adds assume
+// [0, p)); float entries pass unchanged.
+__device__ __forceinline__ uint32_t staged_entry(uint32_t v, uint32_t p) { return v < p ? v : v % p; }
+__device__ __forceinline__ double staged_entry(double v, uint32_t) { return v; }
+__device__ __forceinline__ double2 staged_entry(double2 v, uint32_t) { return v; }
+
 template <typename T>
 __global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
     const StageDesc s = d[blockIdx.x];
     const int n = s.n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        colT[s.dst + (int64_t)j * s.ld + i] = A[s.src + e];
+        colT[s.dst + (int64_t)j * s.ld + i] = staged_entry(A[s.src + e], s.p);
     }
     for (int e = threadIdx.x; e < n * (s.ld - n); e += blockDim.x) {   // zero the padding
         const int j = e / (s.ld - n), i = n + e % (s.ld - n);

@@ -65,12 +65,13 @@ __global__ void noalloc_setup_kernel(const uint32_t* __restrict__ A, const Noall
         reinterpret_cast<uint32_t*>(scratch + kOffPinv)[k] = args.pinv[k];
         reinterpret_cast<unsigned long long*>(scratch + kOffAcc)[k] = 0ull;
     }
-    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
-        const int j = e / ld, i = e % ld;
-        colT[e] = i < n ? A[args.src[k] + (int64_t)i * n + j] : 0u;
-    }
     // Nijenhuis-Wilf column x_i = a_{i,n-1} - (1/2) sum_j a_ij mod p, with 1/2 = (p+1)/2
     const uint64_t p = args.p[k];
+    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+        const int j = e / ld, i = e % ld;
+        const uint32_t a = i < n ? A[args.src[k] + (int64_t)i * n + j] : 0u;
+        colT[e] = a < p ? a : (uint32_t)(a % p);   // residues at or above p taken mod p
+    }
     for (int i = threadIdx.x; i < ld; i += blockDim.x) {
         uint32_t x = 0;
         if (i < n) {

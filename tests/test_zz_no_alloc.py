@@ -62,3 +62,29 @@ def test_noalloc_rejects_oversized_batch():
     rc = _call(px._lib.perm_modp_noalloc, dA, n, off, p, out, torch.cuda.current_stream().cuda_stream)
     assert rc == px.PERMX_EINVAL
     assert "PERMX_NOALLOC_MAX_BATCH" in px.last_error()
+
+
+def test_noalloc_and_batched_take_entries_mod_p():
+    """Residues at or above p are taken mod p while staging, on both entry
+    points: the result is the oracle's permanent of A mod p."""
+    import torch
+
+    import oracle as O
+    import paper_2602_10141_b300 as px
+    lib = px._lib
+    stream = torch.cuda.current_stream().cuda_stream
+    g = np.random.default_rng(11)
+    sizes, primes = [5, 12, 9], [2147483629, 65537, 13]
+    raw = [g.integers(0, 1 << 32, (k, k), dtype=np.uint64).astype(np.uint32) for k in sizes]
+    raw[0] = (raw[0].astype(np.uint64) % primes[0] + primes[0]).astype(np.uint32)   # every entry in [p, 2p)
+    n = np.array(sizes, np.int32)
+    off = np.concatenate([[0], np.cumsum([k * k for k in sizes])[:-1]]).astype(np.int64)
+    flat = np.concatenate([m.reshape(-1) for m in raw]).astype(np.uint32)
+    p = np.array(primes, np.uint32)
+    want = [O.perm_modp_dp((m.astype(np.uint64) % q).astype(np.uint32), q) for m, q in zip(raw, primes)]
+    dA = torch.from_numpy(flat.view(np.int32)).cuda()
+    for fn in (lib.perm_modp, lib.perm_modp_noalloc):
+        out = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+        assert _call(fn, dA, n, off, p, out, stream) == 0, px.last_error()
+        torch.cuda.synchronize()
+        assert [int(x) & 0xFFFFFFFF for x in out.cpu().numpy()] == want
