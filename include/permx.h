@@ -365,6 +365,9 @@ int perm_sample_stats(int field, const void* values, int64_t count, double thres
 
 /* Histogram of |z|^2 (PERMX_HIST_ABS2, formed as in perm_sample_stats), Re z
  * (PERMX_HIST_RE) or Im z (PERMX_HIST_IM) over the `count` device values:
+ * the binned distributions behind the paper's distribution comparisons (§3.2:
+ * |perm U|^2 of Haar unitaries against the exponential law; §5-§7: the
+ * ensembles' Q-Q plots and tail probabilities).  Inputs and outputs:
  * edges = HOST array of nedges strictly increasing doubles (1..4097);
  * counts = DEVICE int64 array of nedges + 1, overwritten: counts[0] values
  * below edges[0], counts[b] values in [edges[b-1], edges[b]), counts[nedges]
