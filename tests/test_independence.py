@@ -55,3 +55,17 @@ def test_nothing_committed_reads_the_working_folder():
             continue
         for ln in _code_lines(p):
             assert "_work/" not in ln and "_work\\\\" not in ln and "'_work'" not in ln and '"_work"' not in ln, (p, ln)
+
+
+def test_package_refuses_to_import_without_its_library(tmp_path):
+    """No fallback: a copy of the package without libpermx.so fails to import."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2602_10141_b300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(PKG, "__init__.py"), pkg / "__init__.py")
+    r = subprocess.run([sys.executable, "-c", "import paper_2602_10141_b300"], cwd=str(tmp_path),
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "is missing" in r.stderr
