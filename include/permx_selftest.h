@@ -1,9 +1,10 @@
 /*
- * Self-test hooks for the integer-mantissa arithmetic of permx's float64 /
+ * Self-test hooks: the integer-mantissa arithmetic of permx's float64 /
  * complex128 walks (the paper has no counterpart; they check this library's
- * own number format).  They run the same host+device helper functions the
- * GPU kernels use, on the CPU, so the arithmetic can be checked against exact
- * big-integer results without a GPU.  They compute no permanents.
+ * own number format) and the batched path's chunk plan.  They run the same
+ * host+device helper functions and the same planner the GPU path uses, on
+ * the CPU, so both can be checked without a GPU (the arithmetic against exact
+ * big-integer results).  They compute no permanents.
  */
 #ifndef PERMX_SELFTEST_H
 #define PERMX_SELFTEST_H
@@ -37,6 +38,22 @@ int permx_x64_accumulate(const int64_t* m, const int32_t* e, const int32_t* neg,
  * not change. */
 int permx_x64_accumulate_merged(const int64_t* m, const int32_t* e, const int32_t* neg, int32_t count,
                                 int32_t parts, int32_t swap, int32_t scale, double* hi, double* lo);
+
+/* The batched path's chunk plan (paper §2.2 Gray-code blocks) for `batch`
+ * matrices of sizes n[0..batch) in field `field` (PERMX_FIELD_*), computed on
+ * the host exactly as perm_c128 / perm_f64 / perm_modp compute it, with no
+ * GPU work.  One row of PERMX_PLAN_COLS int64 per group of equal n, in plan
+ * order: n, ell (log2 Gray steps per chunk), log2_chunks (per matrix), ld
+ * (padded column length), mat_stride (staged elements per matrix), col_off
+ * (first staged element of the group), items (chunks in the group),
+ * partials_per_mat, part_off (first partial slot), x64 (1: integer-mantissa
+ * walk), nmats.  order (host, batch entries) receives the batch indices in
+ * plan order; totals[0] = staged elements, totals[1] = partial slots.
+ * Returns the number of groups, or PERMX_EINVAL (bad field, n or pointer,
+ * more groups than max_groups). */
+#define PERMX_PLAN_COLS 11
+int permx_plan_describe(int field, const int32_t* n, int64_t batch, int64_t* groups, int32_t max_groups,
+                        int64_t* order, int64_t* totals);
 
 #ifdef __cplusplus
 }

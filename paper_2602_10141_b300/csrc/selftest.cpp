@@ -1,6 +1,10 @@
 // CPU entry points for the integer-mantissa helpers (include/permx_selftest.h).
 // They call the very functions the float64 / complex128 kernels inline.
 #include "permx_selftest.h"
+
+#include "batch.h"
+#include "common.cuh"
+#include "permx.h"
 #include "x64_arith.cuh"
 
 using namespace permx;
@@ -81,6 +85,31 @@ int permx_x64_accumulate_merged(const int64_t* m, const int32_t* e, const int32_
         if (a[q].set != a[0].set || (a[0].set && (a[q].acc != a[0].acc || a[q].E != a[0].E))) return -2;
     x64_acc_to_dd(a[0], scale, *hi, *lo);
     return 0;
+}
+
+int permx_plan_describe(int field, const int32_t* n, int64_t batch, int64_t* groups, int32_t max_groups,
+                        int64_t* order, int64_t* totals) {
+    clear_error();
+    if (field != PERMX_FIELD_C128 && field != PERMX_FIELD_F64 && field != PERMX_FIELD_MODP)
+        return fail(PERMX_EINVAL, "unknown field");
+    if (batch < 1 || !n || !groups || !order || !totals || max_groups < 1) return fail(PERMX_EINVAL, "bad arguments");
+    const int max_n = field == PERMX_FIELD_MODP ? PERMX_MAX_N_MODP : PERMX_MAX_N_FP;
+    for (int64_t b = 0; b < batch; ++b)
+        if (n[b] < 1 || n[b] > max_n) return fail(PERMX_EINVAL, "n out of range");
+    const BatchPlan P = plan_batch(n, batch, (Field)field);
+    if ((int64_t)P.groups.size() > max_groups) return fail(PERMX_EINVAL, "more groups than max_groups");
+    int64_t k = 0;
+    for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+        const GroupPlan& g = P.groups[gi];
+        int64_t* row = groups + gi * PERMX_PLAN_COLS;
+        const int64_t v[PERMX_PLAN_COLS] = {g.n, g.ell, g.log2_chunks, g.ld, g.mat_stride, g.col_off, g.items,
+                                            g.partials_per_mat, g.part_off, g.x64 ? 1 : 0, (int64_t)g.mats.size()};
+        for (int c = 0; c < PERMX_PLAN_COLS; ++c) row[c] = v[c];
+        for (int64_t m : g.mats) order[k++] = m;
+    }
+    totals[0] = P.col_elems;
+    totals[1] = P.total_partials;
+    return (int)P.groups.size();
 }
 
 }  // extern "C"
