@@ -1,10 +1,10 @@
-"""Writes schur_crt_oracle.txt: exact perm(S_n) for n = 21..29 computed by the
+"""Writes schur_crt_oracle.txt: exact perm(S_n) for n = 21..31 computed by the
 oracle alone (plain Ryser mod p in binary subset order, row sums recomputed for
 every subset, then Chinese remaindering in Python integers; paper §2.1 method),
 with one extra prime as a check and the bound |perm(S_n)|^2 <= n^n asserted.
 It calls nothing but the oracle.  Run from the repository root:
-    python tests/golden/make_schur_crt.py            # every n (about 25 minutes on 8 cores)
-    python tests/golden/make_schur_crt.py 28 29      # only these n; the other rows are kept
+    python tests/golden/make_schur_crt.py            # every n (about 2 hours on 8 cores)
+    python tests/golden/make_schur_crt.py 30 31      # only these n; the other rows are kept
 """
 import os
 import sys
@@ -15,7 +15,7 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 
 
-NS = range(21, 30)
+NS = range(21, 32)
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schur_crt_oracle.txt")
 
 

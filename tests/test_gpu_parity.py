@@ -382,11 +382,11 @@ def test_n1_all_fields(px, arith):
 
 def test_schur_crt_matches_oracle_fixture(px):
     """Exact perm(S_n) for every n of tests/golden/schur_crt_oracle.txt (written
-    by make_schur_crt.py from the oracle alone; n = 21..29 at least), through
+    by make_schur_crt.py from the oracle alone; n = 21..31), through
     the GPU F_p walk and the library's CRT, equals the oracle's value."""
     from conftest import read_golden
     rows = read_golden("schur_crt_oracle.txt")
-    assert set(range(21, 30)) <= {int(r[0]) for r in rows}
+    assert set(range(21, 32)) <= {int(r[0]) for r in rows}
     for r in rows:
         n, value = int(r[0]), int(r[1])
         assert px.perm_schur_crt(n) == value, n

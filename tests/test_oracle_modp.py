@@ -172,7 +172,7 @@ def test_crt_recovers_schur_with_disjoint_prime_sets():
 
 
 def test_schur_crt_fixture_consistent():
-    """The stored oracle values of perm(S_n) (n = 21..29) agree with the oracle's
+    """The stored oracle values of perm(S_n) (n = 21..31) agree with the oracle's
     F_p Ryser modulo a prime that the generator did not use (n = 21, 22, 23)
     and respect |perm(S_n)|^2 <= n^n."""
     import os
