@@ -191,17 +191,24 @@ def cpu_baseline(primes, mats, target_s: float = 16.0):
     O.ryser_modp_gray_range(A, p, k0, k0 + span1)
     dt1 = time.perf_counter() - t1
     O.set_num_threads(cores)
-    # the paper's own CPU algorithm (incremental Gray walk, one thread), the
-    # comparator for its GPU-over-single-threaded-CPU speed-ups: about 4 s
+    # the paper's own CPU algorithm (incremental Gray walk), the comparator for
+    # its GPU-over-CPU speed-ups: on one thread (its single-threaded figure)
+    # and with one Gray block per host core (its multi-core figure), each for
+    # about target_s / 4 seconds
     from oracle import cpu_walk as W
-    W.modp_gray_range(A, p, k0, k0 + (1 << 16))
+    walk_s = target_s / 4
+    W.modp_gray_range(A, p, k0, k0 + (1 << 14))
     t2 = time.perf_counter()
-    W.modp_gray_range(A, p, k0, k0 + (1 << 18))
-    rate_w = (1 << 18) / max(time.perf_counter() - t2, 1e-9)
-    span_w = int(min(max(rate_w * 4.0, 1 << 18), 1 << 30))
+    W.modp_gray_range(A, p, k0, k0 + (1 << 16))
+    rate_w = (1 << 16) / max(time.perf_counter() - t2, 1e-9)
+    span_w = int(min(max(rate_w * walk_s, 1 << 16), 1 << 30))
     t2 = time.perf_counter()
     W.modp_gray_range(A, p, k0, k0 + span_w)
     dt2 = time.perf_counter() - t2
+    span_m = int(min(span_w * max(cores, 1), 1 << 31))
+    t3 = time.perf_counter()
+    _, threads_m = W.modp_gray_range_mt(A, p, k0, k0 + span_m)
+    dt3 = time.perf_counter() - t3
     return {"value": N * span / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"Gray indices [{k0}, {k0 + span}) of S_33 mod {p} (one of 5 primes), "
                       f"{span} subsets x {N} rows, {dt:.1f} s",
@@ -209,7 +216,10 @@ def cpu_baseline(primes, mats, target_s: float = 16.0):
                             "sample": f"Gray indices [{k0}, {k0 + span1}), {dt1:.1f} s"},
             "gray_walk_single_core": {"value": N * span_w / dt2, "unit": UNIT, "cores": 1,
                                       "kind": "plain CPU Gray-code walk (incremental row sums, uint64 %)",
-                                      "sample": f"Gray indices [{k0}, {k0 + span_w}), {dt2:.1f} s"}}
+                                      "sample": f"Gray indices [{k0}, {k0 + span_w}), {dt2:.1f} s"},
+            "gray_walk_all_cores": {"value": N * span_m / dt3, "unit": UNIT, "cores": threads_m,
+                                    "kind": "the same walk, one contiguous Gray block per host thread",
+                                    "sample": f"Gray indices [{k0}, {k0 + span_m}), {dt3:.1f} s"}}
 
 
 def run_reference(args, rank, world):

@@ -1,5 +1,5 @@
 /*
- * Single-threaded CPU Gray-code Ryser walks — BENCHMARK / TEST INFRASTRUCTURE
+ * Plain CPU Gray-code Ryser walks — BENCHMARK / TEST INFRASTRUCTURE
  * ONLY (the same rule as oracle.c: only tests/ and the cpu_baseline leg of
  * bench.py load this library; the CUDA product never links, loads or calls
  * it, and it shares no header, helper or constant with the product).
@@ -17,9 +17,14 @@
  *
  * Arithmetic is the plainest of each kind: uint64 with '%' for F_p (paper
  * §2.1), IEEE double (or complex double) with no compensation for R and C.
- * No threads, no SIMD intrinsics, no blocking: the compiler's -O2 only.
+ * No SIMD intrinsics, no blocking: the compiler's -O2 only.  The walks run on
+ * one thread; cpuwalk_modp_gray_range_mt splits a range into one contiguous
+ * Gray block per OpenMP thread (paper §2.2, as the paper's multi-core CPU
+ * comparison does), each walked by the one-thread code.
  */
+#include <omp.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 static int ctz64(uint64_t x) { return __builtin_ctzll(x); }
 
@@ -55,6 +60,32 @@ int cpuwalk_modp_gray_range(int n, const uint32_t* A, uint32_t p, uint64_t k0, u
     }
     *out = (uint32_t)((pos + pp - neg) % pp);
     return 0;
+}
+
+/* The same sum with the range cut into one contiguous block per OpenMP
+ * thread; the block sums are added mod p in block order.  Returns the number
+ * of threads used (>= 1) or -1. */
+int cpuwalk_modp_gray_range_mt(int n, const uint32_t* A, uint32_t p, uint64_t k0, uint64_t k1, uint32_t* out) {
+    if (n < 1 || n > 63 || !A || !out || p < 2 || k0 > k1 || k1 > (1ull << n)) return -1;
+    const int nt = omp_get_max_threads();
+    uint32_t* part = (uint32_t*)calloc((size_t)nt, sizeof(uint32_t));
+    if (!part) return -1;
+    const uint64_t len = k1 - k0;
+    int rc = 0;
+    #pragma omp parallel num_threads(nt) reduction(|:rc)
+    {
+        const int t = omp_get_thread_num();
+        const uint64_t q = len / (uint64_t)nt, r = len % (uint64_t)nt;   // the first r blocks get one more
+        const uint64_t a = k0 + q * (uint64_t)t + ((uint64_t)t < r ? (uint64_t)t : r);
+        const uint64_t b = a + q + ((uint64_t)t < r ? 1 : 0);
+        rc |= cpuwalk_modp_gray_range(n, A, p, a, b, &part[t]) != 0;
+    }
+    uint64_t s = 0;
+    for (int t = 0; t < nt; ++t) s = (s + part[t]) % p;
+    free(part);
+    if (rc) return -1;
+    *out = (uint32_t)s;
+    return nt;
 }
 
 /* The same signed sum over real entries in plain double (no (-1)^n factor). */

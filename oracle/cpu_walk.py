@@ -1,4 +1,4 @@
-"""Single-threaded CPU Gray-code Ryser walks — BENCHMARK / TEST INFRASTRUCTURE ONLY.
+"""Plain CPU Gray-code Ryser walks — BENCHMARK / TEST INFRASTRUCTURE ONLY.
 
 The paper's §2.2 algorithm as a plain one-core program (``cpu_walk.c``): row
 sums kept and updated by one column per Gray step, uint64 ``%`` for F_p,
@@ -24,9 +24,9 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``cpu_walk.c`` into ``libcpuwalk.so`` (gcc -O2, no threads)."""
+    """Compile ``cpu_walk.c`` into ``libcpuwalk.so`` (gcc -O2; OpenMP only for the block-split F_p walk)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
                "-o", _LIB + ".tmp", _SRC]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
@@ -42,9 +42,11 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         lib.cpuwalk_modp_gray_range.argtypes = [i, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32, u64, u64,
                                                 ctypes.POINTER(ctypes.c_uint32)]
+        lib.cpuwalk_modp_gray_range_mt.argtypes = lib.cpuwalk_modp_gray_range.argtypes
         lib.cpuwalk_f64_gray_range.argtypes = [i, dp, u64, u64, dp]
         lib.cpuwalk_c128_gray_range.argtypes = [i, dp, u64, u64, dp]
-        for f in (lib.cpuwalk_modp_gray_range, lib.cpuwalk_f64_gray_range, lib.cpuwalk_c128_gray_range):
+        for f in (lib.cpuwalk_modp_gray_range, lib.cpuwalk_modp_gray_range_mt, lib.cpuwalk_f64_gray_range,
+                  lib.cpuwalk_c128_gray_range):
             f.restype = i
         _lib = lib
     return _lib
@@ -68,6 +70,19 @@ def modp_gray_range(A, p: int, k0: int, k1: int) -> int:
     if rc != 0:
         raise ValueError(f"cpuwalk_modp_gray_range: bad arguments (rc {rc})")
     return int(out[0])
+
+
+def modp_gray_range_mt(A, p: int, k0: int, k1: int) -> tuple[int, int]:
+    """modp_gray_range with one contiguous Gray block per OpenMP thread:
+    (the same residue, the number of threads used)."""
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.uint32))
+    n = _square(a)
+    out = np.zeros(1, np.uint32)
+    rc = _load().cpuwalk_modp_gray_range_mt(n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(p), int(k0),
+                                            int(k1), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    if rc < 1:
+        raise ValueError(f"cpuwalk_modp_gray_range_mt: bad arguments (rc {rc})")
+    return int(out[0]), int(rc)
 
 
 def fp_gray_range(A, k0: int, k1: int):

@@ -55,3 +55,19 @@ def test_jsonl_log_copies_the_result_line(tmp_path):
         assert rec["impl"] == "reference" and rec["metric"] == printed[0]["metric"]
         assert rec["logged_at"] and "--jsonl" in rec["argv"]
     assert "logged_at" not in printed[0]
+
+
+def test_cpu_baseline_on_the_host():
+    """bench.py's cpu_baseline leg runs on the CPU alone: the oracle on all
+    cores and on one, and the plain Gray walk on one thread and on all."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle as O
+    n = 33
+    primes = O.primes_1_mod_n(n, 1)
+    mats = [O.schur_residue_matrix(n, p, O.primitive_nth_root(p, n)) for p in primes]
+    cb = bench.cpu_baseline(primes, mats, target_s=0.4)
+    assert cb["kind"] == "oracle" and cb["unit"] == "terms/s" and cb["value"] > 0 and cb["cores"] >= 1
+    for key in ("single_core", "gray_walk_single_core", "gray_walk_all_cores"):
+        assert cb[key]["value"] > 0 and cb[key]["cores"] >= 1 and cb[key]["sample"], key
+    assert cb["gray_walk_all_cores"]["cores"] == cb["cores"]

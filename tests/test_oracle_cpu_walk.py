@@ -129,10 +129,12 @@ def test_walk_planted_mistake_is_caught(tmp_path, desc, old, new):
     mutated = tmp_path / "cpu_walk_planted.c"
     mutated.write_text(src.replace(old, new))
     so = tmp_path / "libcpuwalk_planted.so"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-w", "-o", str(so), str(mutated)])
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-w", "-o", str(so),
+                           str(mutated)])
     saved = W._load()
     lib = ctypes.CDLL(str(so))
-    for name in ("cpuwalk_modp_gray_range", "cpuwalk_f64_gray_range", "cpuwalk_c128_gray_range"):
+    for name in ("cpuwalk_modp_gray_range", "cpuwalk_modp_gray_range_mt", "cpuwalk_f64_gray_range",
+                 "cpuwalk_c128_gray_range"):
         getattr(lib, name).argtypes = getattr(saved, name).argtypes
         getattr(lib, name).restype = getattr(saved, name).restype
     W._lib = lib
@@ -141,3 +143,17 @@ def test_walk_planted_mistake_is_caught(tmp_path, desc, old, new):
     finally:
         W._lib = saved
     assert failed, f"planted mistake not caught: {desc}"
+
+
+@pytest.mark.parametrize("span", [0, 1, 3, 7, 8, 9, 1000, 40000])
+def test_block_split_walk_equals_one_thread_walk(span):
+    """One contiguous Gray block per OpenMP thread (paper §2.2) gives the
+    one-thread walk's residue, also when the range is shorter than the
+    thread count (empty blocks)."""
+    n, p = 16, 2147483629
+    g = rng(990 + span)
+    A = g.integers(0, p, size=(n, n), dtype=np.uint64).astype(np.uint32)
+    k0 = int(g.integers(0, (1 << n) - span + 1))
+    got, threads = W.modp_gray_range_mt(A, p, k0, k0 + span)
+    assert threads >= 1
+    assert got == W.modp_gray_range(A, p, k0, k0 + span) == O.ryser_modp_gray_range(A, p, k0, k0 + span)
