@@ -52,6 +52,15 @@ int permx_x64_accumulate_merged(const int64_t* m, const int32_t* e, const int32_
  * Returns the number of groups, or PERMX_EINVAL (bad field, n or pointer,
  * more groups than max_groups). */
 #define PERMX_PLAN_COLS 11
+
+/* The serving arena (admission by device memory, serve_*) on its own, on the
+ * host: an arena of `capacity` bytes runs `nops` operations ops[2k], ops[2k+1]:
+ * (0, bytes) allocates and records results[3k] = offset or -1; (1, j)
+ * releases the block allocated by operation j (which must have succeeded and
+ * not been released).  After each operation results[3k+1] = bytes in use and
+ * results[3k+2] = the largest free block.  Returns the number of free blocks
+ * at the end, or PERMX_EINVAL for a bad operation. */
+int permx_arena_run(int64_t capacity, const int64_t* ops, int32_t nops, int64_t* results);
 int permx_plan_describe(int field, const int32_t* n, int64_t batch, int64_t* groups, int32_t max_groups,
                         int64_t* order, int64_t* totals);
 

@@ -2,6 +2,9 @@
 // They call the very functions the float64 / complex128 kernels inline.
 #include "permx_selftest.h"
 
+#include <vector>
+
+#include "arena.h"
 #include "batch.h"
 #include "common.cuh"
 #include "permx.h"
@@ -110,6 +113,32 @@ int permx_plan_describe(int field, const int32_t* n, int64_t batch, int64_t* gro
     totals[0] = P.col_elems;
     totals[1] = P.total_partials;
     return (int)P.groups.size();
+}
+
+int permx_arena_run(int64_t capacity, const int64_t* ops, int32_t nops, int64_t* results) {
+    clear_error();
+    if (capacity < 0 || nops < 0 || (nops > 0 && (!ops || !results))) return fail(PERMX_EINVAL, "bad arguments");
+    Arena a;
+    a.reset((size_t)capacity);
+    std::vector<int64_t> size_of(nops, -1);   // bytes of each live block, by allocating operation
+    for (int32_t k = 0; k < nops; ++k) {
+        const int64_t kind = ops[2 * k], v = ops[2 * k + 1];
+        if (kind == 0) {
+            if (v < 0) return fail(PERMX_EINVAL, "negative size");
+            results[3 * k] = a.alloc((size_t)v);
+            if (results[3 * k] >= 0) size_of[k] = v;
+        } else if (kind == 1) {
+            if (v < 0 || v >= k || ops[2 * v] != 0 || size_of[v] < 0) return fail(PERMX_EINVAL, "bad release");
+            a.release((size_t)results[3 * v], (size_t)size_of[v]);
+            size_of[v] = -1;
+            results[3 * k] = 0;
+        } else {
+            return fail(PERMX_EINVAL, "unknown operation");
+        }
+        results[3 * k + 1] = (int64_t)a.used();
+        results[3 * k + 2] = (int64_t)a.largest_free();
+    }
+    return (int)a.free_blocks();
 }
 
 }  // extern "C"

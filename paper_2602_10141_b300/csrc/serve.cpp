@@ -30,6 +30,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "batch.h"
 #include "common.cuh"
 #include "permx.h"
@@ -43,51 +44,6 @@ int64_t now_ns() {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// first-fit allocator over a byte range
-class Arena {
-public:
-    void reset(size_t bytes) {
-        free_.clear();
-        if (bytes) free_[0] = bytes;
-        used_ = 0;
-    }
-    int64_t alloc(size_t bytes) {
-        bytes = align256(bytes);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                const size_t off = it->first, len = it->second;
-                free_.erase(it);
-                if (len > bytes) free_[off + bytes] = len - bytes;
-                used_ += bytes;
-                return (int64_t)off;
-            }
-        }
-        return -1;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = align256(bytes);
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-
-private:
-    std::map<size_t, size_t> free_;
-    size_t used_ = 0;
-};
 
 struct Request {
     uint64_t ticket = 0;
