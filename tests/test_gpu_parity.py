@@ -405,3 +405,19 @@ def test_schur_crt_disjoint_primes_match_fixture(px):
         got, residues = px.perm_schur_crt_primes(n, disjoint)
         assert got == value, n
         assert residues[-1] == value % disjoint[-1]
+
+
+def test_schur33_benchmark_launch_matches_oracle_residue(px):
+    """Full-size parity in the benchmark's launch configuration: the five S_33
+    residue matrices in one batched perm_modp call (the Nijenhuis-Wilf walk the
+    benchmark times) give, for the first prime, the residue the oracle computed
+    over all 2^33 subsets (tests/golden/schur33_residue.txt, written by
+    make_schur33_residue.py from the oracle alone).  perm(S_33) mod p does not
+    depend on the primitive root chosen."""
+    from conftest import read_golden
+    n, p, _, r = (int(x) for x in read_golden("schur33_residue.txt")[0])
+    primes = O.primes_1_mod_n(n, 5)
+    assert primes[0] == p
+    mats = [O.schur_residue_matrix(n, q, O.primitive_nth_root(q, n)) for q in primes]
+    got = run_modp(px, mats, primes)
+    assert int(got[0]) == r
