@@ -41,9 +41,12 @@ NPRIMES = 5
 METRIC = "ryser_terms_per_s"
 UNIT = "terms/s"
 WORKLOAD = "schur_n33_fp_5primes"
-# dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch of this
-# command, from a one-pass ncu capture at full size of the current kernel
-WALK_DRAM_BYTES_PER_LAUNCH = 963840
+# dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch over the
+# 2^30-step small case (bench.py --profile-case, one ncu pass), scaled by the steps of a
+# bench launch (5 x 2^32): the traffic is the residue tables and instruction fetch, and
+# grows with the launch's length; see profiles/ryser_modp_n33_schur.md
+WALK_DRAM_BYTES_SMALL_CASE = 36_000
+WALK_DRAM_BYTES_PER_LAUNCH = WALK_DRAM_BYTES_SMALL_CASE * (NPRIMES * 2 ** 32) // 2 ** 30
 
 
 def _rank_env():
@@ -209,6 +212,11 @@ def cpu_baseline(primes, mats, target_s: float = 16.0):
     t3 = time.perf_counter()
     _, threads_m = W.modp_gray_range_mt(A, p, k0, k0 + span_m)
     dt3 = time.perf_counter() - t3
+    # the block split of the multi-core walk, checked against the oracle on a short range
+    ka = k0 + (1 << 29) + 12345
+    mt_ok = W.modp_gray_range_mt(A, p, ka, ka + (1 << 20) + 7)[0] == O.ryser_modp_gray_range(A, p, ka,
+                                                                                             ka + (1 << 20) + 7)
+    assert mt_ok, "multi-core CPU walk disagrees with the oracle"
     return {"value": N * span / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"Gray indices [{k0}, {k0 + span}) of S_33 mod {p} (one of 5 primes), "
                       f"{span} subsets x {N} rows, {dt:.1f} s",
@@ -218,6 +226,7 @@ def cpu_baseline(primes, mats, target_s: float = 16.0):
                                       "kind": "plain CPU Gray-code walk (incremental row sums, uint64 %)",
                                       "sample": f"Gray indices [{k0}, {k0 + span_w}), {dt2:.1f} s"},
             "gray_walk_all_cores": {"value": N * span_m / dt3, "unit": UNIT, "cores": threads_m,
+                                    "checked_against_oracle": f"Gray indices [{ka}, {ka + (1 << 20) + 7})",
                                     "kind": "the same walk, one contiguous Gray block per host thread",
                                     "sample": f"Gray indices [{k0}, {k0 + span_m}), {dt3:.1f} s"}}
 
@@ -256,6 +265,22 @@ def run_reference(args, rank, world):
     return 0
 
 
+def multiply_pipe_bound(px, sms: int) -> dict:
+    """Evaluated terms/s that the F_p walk's multiplies allow on this GPU now:
+    a term needs one mul.wide, one mul.lo and one mul.hi (signed Montgomery
+    product), all on the integer-multiply pipe, so the bound is
+    1 / (1/R_wide + 1/R_lo + 1/R_hi) with each R the whole-GPU issue rate the
+    library's probe kernels measure (8 independent chains per thread, 8
+    blocks of 256 threads per SM)."""
+    rates = {}
+    for name, kind in (("mul_wide_u32", 5), ("mad_lo_u32", 4), ("mul_hi_u32", 6)):
+        px.permx_peak_probe(kind, sms * 8, 256, 1024)            # warm-up
+        ops, ms = px.permx_peak_probe(kind, sms * 8, 256, 8192)
+        rates[name] = ops
+    bound = 1.0 / sum(1.0 / r for r in rates.values())
+    return {"bound_terms_per_s": bound, "rates_ops_per_s": rates}
+
+
 def run_profile_case():
     import torch
     import paper_2602_10141_b300 as px
@@ -292,6 +317,10 @@ def main():
                     help="ensembles_batched / serving: fraction of the full sample counts")
     ap.add_argument("--jsonl", default="",
                     help="also append every JSON result line (with a timestamp and the arguments) to this file")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the plain, batched and served measurements added to the line")
+    ap.add_argument("--extras-scale", type=float, default=1.0,
+                    help="fraction of the full sample counts for the batched and served measurements")
     args = ap.parse_args()
     rank, world, local = _rank_env()
     if args.jsonl and rank == 0:
@@ -333,6 +362,8 @@ def main():
         step()
     torch.cuda.synchronize()
     value_ref = crt_of(out.cpu().numpy())
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    bound = multiply_pipe_bound(px, sms)
 
     # timed region: per-step CUDA events, L2 flushed between steps (outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -375,15 +406,20 @@ def main():
         dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
     e2e_value = units_per_step * args.steps * world / float(t_e2e.item())
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        # the batched, plain and served halves of the metric, each with its own clock record
+        import bench_workloads as BW
+        extras["plain"] = BW.plain_object()
+        extras["batched"] = BW.batched_object(args.extras_scale)
+        extras["served"] = BW.served_object(args.extras_scale)
+
     if rank == 0:
-        peaks = measured_peaks()
         # integer-issue roofline of the F_p walk: one term = 1 modular add + 1 Montgomery
-        # multiply; the IMAD pipe (mul.wide + mul.lo + mul.hi per term) binds at
-        # 148 SMs x clock x 12.4 terms/clk/SM (per-instruction rates measured with the
-        # library's issue-rate probes); the clock is the median sampled under load.
+        # multiply; the multiply pipe (mul.wide + mul.lo + mul.hi per term) binds, at the
+        # rates the library's probes measured on this GPU just before the timed region
         cs = clk.summary()
-        mhz = cs["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
-        peak = 148 * mhz * 1e6 * 12.4
+        peak = bound["bound_terms_per_s"]
         achieved = evaluated_per_step / (statistics.median(ms) / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -397,15 +433,18 @@ def main():
             "terms_evaluated_per_s": evaluated_per_step * args.steps * world / t_max,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tterms/s",
                          "frac": achieved / peak, "traffic": WALK_DRAM_BYTES_PER_LAUNCH,
-                         "traffic_unit": "bytes per launch",
+                         "traffic_unit": "bytes per launch (small-case capture scaled to the launch)",
                          "kernel": f"ryser_modp_kernel<{N}>",
-                         "peak_source": "IMAD-pipe bound from measured per-instruction rates x sampled SM clock"},
+                         "peak_source": "integer-multiply-pipe bound 1/(1/R_wide + 1/R_lo + 1/R_hi) from the "
+                                        "library's issue-rate probes run in this process (permx_peak_probe)",
+                         "probe_rates_ops_per_s": bound["rates_ops_per_s"]},
             "clocks": cs,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
                     "d2h_bytes_per_step": 4 * NPRIMES},
             "gpu_launches": 4 * args.steps,   # metadata, staging, Gray walk, finalize per step
             "device": device_info(torch, local),
         }
+        line.update(extras)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(primes, mats)
         print(json.dumps(line), flush=True)

@@ -23,12 +23,10 @@ continuous-batching server, each printed as one JSON line.
 """
 from __future__ import annotations
 
-import ctypes
 import json
 import math
 import os
 import statistics
-import struct
 import time
 
 import numpy as np
@@ -277,7 +275,20 @@ def profile_stats(args):
     return 0
 
 
-def haar14_plain(args):
+def _clocked(fn, *a, **k):
+    """Run fn under the nvidia-smi clock sampler; returns (fn's dict, clocks)."""
+    from bench import ClockSampler
+    import torch
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        out = fn(*a, **k)
+    return out, clk.summary()
+
+
+def plain_object(steps: int = 5, warmup: int = 3) -> dict:
+    """Config 1: 256 Haar-random U(14), complex128, seed 0 (QR of complex
+    Ginibre N(0,1/2)+iN(0,1/2), R's phases folded in), one matrix per
+    perm_c128 call, against one batched call of all 256 and one CUDA-graph
+    replay per matrix; a sample is checked against the oracle."""
     import torch
 
     import oracle as O
@@ -289,235 +300,305 @@ def haar14_plain(args):
     n1 = np.array([14], np.int32)
     offs = [np.array([i * 196], np.int64) for i in range(256)]
     nb, ob = np.full(256, 14, np.int32), np.arange(256, dtype=np.int64) * 196
+    stream = torch.cuda.current_stream()
 
     def plain():
         for i in range(256):
-            px.perm_c128(A, n1, offs[i], out[i:i + 1])
+            px.perm_c128(A, n1, offs[i], out[i:i + 1], stream)
 
     def batched():
-        px.perm_c128(A, nb, ob, out)
+        px.perm_c128(A, nb, ob, out, stream)
 
-    # one matrix per launch, each a replayed CUDA graph of its own plan (captured at warm-up)
     plans = [px.Plan(px.FIELD_C128, n1, np.zeros(1, np.int64)) for _ in range(256)]
     views = [(A[i * 196:], out[i:i + 1]) for i in range(256)]
 
     def plain_graph():
         for pl, (a, o) in zip(plans, views):
-            pl.graph_launch(a, o)
+            pl.graph_launch(a, o, stream)
 
-    res = {}
-    for name, fn in (("plain", plain), ("batched", batched), ("plain_graph", plain_graph)):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(args.steps):
-            a, b = _events(torch)
-            a.record()
-            fn()
-            b.record()
+    def timed():
+        res = {}
+        for name, fn in (("plain", plain), ("batched", batched), ("plain_graph", plain_graph)):
+            for _ in range(warmup):
+                fn()
             torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        res[name] = statistics.median(ms)
+            ms = []
+            for _ in range(steps):
+                a, b = _events(torch)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            res[name] = statistics.median(ms)
+        return res
+
+    res, clocks = _clocked(timed)
     for pl in plans:
         pl.close()
+    px.perm_c128(A, nb, ob, out, stream)
     got = out.cpu().numpy()
-    worst = max(abs(got[i] - O.perm_dp(mats[i])) / abs(O.perm_dp(mats[i])) for i in range(0, 256, 32))
+    worst = max(abs(got[i] - O.perm_dp(mats[i])) / abs(O.perm_dp(mats[i])) for i in range(0, 256, 16))
     terms = 256 * 14 * 2.0 ** 14
-    # the paper's CPU algorithm on one core (plain double Gray walk) over the same 256 matrices
     from oracle import cpu_walk as W
     t_w = time.perf_counter()
     for i in range(256):
         W.perm(mats[i])
     walk_s = time.perf_counter() - t_w
-    line = {"workload": "haar14_plain", "metric": "perms_per_s", "value": 256 / (res["plain"] / 1e3),
-            "unit": "perm/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["plain"], "batched_perms_per_s": 256 / (res["batched"] / 1e3),
-            "batched_ms": res["batched"], "nominal_terms_per_s_plain": terms / (res["plain"] / 1e3),
-            "nominal_terms_per_s_batched": terms / (res["batched"] / 1e3),
+    return {"metric": "perms_per_s", "value": 256 / (res["plain"] / 1e3), "unit": "perm/s",
+            "higher_is_better": True, "steps": steps, "warmup": warmup, "ms_per_step": res["plain"],
+            "batched_perms_per_s": 256 / (res["batched"] / 1e3), "batched_ms": res["batched"],
+            "batched_over_plain": res["plain"] / res["batched"],
             "plain_graph_perms_per_s": 256 / (res["plain_graph"] / 1e3), "plain_graph_ms": res["plain_graph"],
-            "kernels_per_call": 4, "graph_launches_plain_graph": 256,
-            "max_rel_err_vs_oracle_sample": worst, "dtype": "c128",
+            "nominal_terms_per_s_plain": terms / (res["plain"] / 1e3),
+            "nominal_terms_per_s_batched": terms / (res["batched"] / 1e3),
+            "max_rel_err_vs_oracle_sample": worst, "oracle_checked": 16, "dtype": "c128",
+            "clocks": clocks,
             "cpu_gray_walk_single_core": {"value": 256 / walk_s, "unit": "perm/s", "cores": 1,
-                                          "nominal_terms_per_s": terms / walk_s,
                                           "kind": "plain CPU Gray-code walk (uncompensated complex double)",
                                           "sample": f"the same 256 matrices, {walk_s:.2f} s"},
-            "config": {"n": 14, "count": 256, "ensemble": "haar_u", "seed": 0}}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": "haar_u14_c128_256_one_per_call", "n": 14, "count": 256, "ensemble": "haar_u",
+                       "seed": 0, "timing": f"median of {steps} passes after {warmup} warm-up passes, CUDA events"}}
+
+
+def haar14_plain(args):
+    d = plain_object(args.steps, args.warmup)
+    d["workload"] = "haar14_plain"
+    print(json.dumps(d), flush=True)
     return 0
 
 
-def ensembles_batched(args):
+def _ensemble_inputs(count: int, seed0: int = 0):
+    """Device inputs of the ragged batch: per field one flat tensor with
+    `count` matrices of each (ensemble, n), grouped by ensemble then n."""
     import torch
 
-    import oracle as O
-    import paper_2602_10141_b300 as px
     from workloads import device as D
-    count = max(2, int(round(50000 * args.scale)))
     fields = {}
     for cplx, names in ((True, CPLX), (False, REAL)):
         parts, ns = [], []
         for ei, name in enumerate(names):
             for n in SIZES:
-                t = D.batch(name, n, count, seed=1000 * (ei + 1) + n + (0 if cplx else 500))
+                t = D.batch(name, n, count, seed=seed0 + 1000 * (ei + 1) + n + (0 if cplx else 500))
                 parts.append(t.reshape(-1))
                 ns += [n] * count
         flat = torch.cat(parts)
+        del parts
         ns = np.array(ns, np.int32)
         offs = np.concatenate([[0], np.cumsum(ns.astype(np.int64) ** 2)[:-1]]).astype(np.int64)
         out = torch.empty(len(ns), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
         fields[cplx] = (flat, ns, offs, out)
+    return fields
+
+
+def _graph_for(px, fields):
+    plans = [px.Plan(px.FIELD_C128 if cplx else px.FIELD_F64, ns, offs) for cplx, (_, ns, offs, _) in fields.items()]
+    g = px.Graph(plans, [v[0] for v in fields.values()], [v[3] for v in fields.values()])
+    return plans, g
+
+
+def _close(plans, g):
+    g.close()
+    for pl in plans:
+        pl.close()
+
+
+def _tune_batch(n: int) -> int:
+    """Matrices per autotuning pass: about 2^21 Gray chunks (the built-in chunking
+    cuts a walk of n - 1 bits into 2^min(14, n - 4) chunks), at most 8192."""
+    chunks = 2 ** min(14, max(n - 4, 0))
+    return int(max(64, min(8192, 2 ** 21 // chunks)))
+
+
+def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
+    """Config 3: 50,000 matrices (x scale) of each of six ensembles at each n in
+    {8, 12, 16, 20, 23}: Haar U, GUE, complex Ginibre (complex128) and Haar O,
+    GOE, real Ginibre (float64), generated on the device.  The chunk length of
+    every (field, n) is picked by perm_autotune; both fields' plans are
+    captured into ONE CUDA graph (every size group a parallel branch) and the
+    step is one replay of that graph, timed with CUDA events on the launching
+    stream.  Per size, the same ensembles at scale/10 through their own graph
+    and one perm_c128 / perm_f64 call per matrix on 8 matrices of every
+    (ensemble, n) give the batched-vs-plain comparison.  One matrix of every
+    (ensemble, n) is checked against the oracle."""
+    import tempfile
+
+    import torch
+
+    import oracle as O
+    import paper_2602_10141_b300 as px
+    count = max(2, int(round(50000 * scale)))
+    stream = torch.cuda.current_stream()
+    fields_keys = {True: px.FIELD_C128, False: px.FIELD_F64}
+    # 1) chunk lengths, autotuned on synthetic batches, kept in a tuning file
+    t0 = time.perf_counter()
+    table = {}
+    for cplx, field in fields_keys.items():
+        for n in SIZES:
+            if tune:
+                table[f"{'c128' if cplx else 'f64'}:{n}"] = px.perm_autotune(field, n, _tune_batch(n), 3)
+            else:
+                table[f"{'c128' if cplx else 'f64'}:{n}"] = px.perm_tune_get(field, n)
+    tune_s = time.perf_counter() - t0
+    tune_path = os.path.join(tempfile.gettempdir(), f"permx_tune_{os.getpid()}.txt")
+    px.perm_tune_save(tune_path)
+    # 2) inputs on the device
+    t0 = time.perf_counter()
+    fields = _ensemble_inputs(count)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    input_bytes = sum(v[0].numel() * v[0].element_size() for v in fields.values())
     total_perms = sum(len(v[1]) for v in fields.values())
     total_terms = sum(nominal_terms(v[1]) for v in fields.values())
-
-    def step():
-        for cplx, (flat, ns, offs, out) in fields.items():
-            (px.perm_c128 if cplx else px.perm_f64)(flat, ns, offs, out)
-
-    for _ in range(args.warmup):
-        step()
+    eval_terms = sum(float(np.sum(v[1].astype(np.float64) * 2.0 ** (v[1] - 1))) for v in fields.values())
+    # 3) warm-up: a small graph of the same kernels, then capture the full one
+    small = _ensemble_inputs(max(2, count // 1000), seed0=77)
+    pl_s, g_s = _graph_for(px, small)
+    g_s.launch(stream)
     torch.cuda.synchronize()
-    ms = []
-    for _ in range(args.steps):
-        a, b = _events(torch)
-        a.record()
-        step()
-        b.record()
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    t = statistics.median(ms) / 1e3
+    _close(pl_s, g_s)
+    del small
+    plans, graph = _graph_for(px, fields)
 
-    # plain: one call per matrix on a subsample of 8 per (field, ensemble, n)
-    plain_perms, plain_terms, plain_ms = 0, 0.0, 0.0
-    for cplx, (flat, ns, offs, out) in fields.items():
-        fn = px.perm_c128 if cplx else px.perm_f64
-        idx = [g * count + k for g in range(len(ns) // count) for k in range(8)]
-        for i in idx[:2]:
-            fn(flat, ns[i:i + 1], offs[i:i + 1], out[i:i + 1])
-        torch.cuda.synchronize()
+    def timed():
         a, b = _events(torch)
-        a.record()
-        for i in idx:
-            fn(flat, ns[i:i + 1], offs[i:i + 1], out[i:i + 1])
-        b.record()
+        a.record(stream)
+        graph.launch(stream)
+        b.record(stream)
         torch.cuda.synchronize()
-        plain_ms += a.elapsed_time(b)
-        plain_perms += len(idx)
-        plain_terms += nominal_terms(ns[idx])
-    step()
-    torch.cuda.synchronize()
+        return a.elapsed_time(b)
 
-    # oracle check on a seeded subsample (n <= 16), and the oracle's Ryser rate
-    # (double-double, row sums recomputed per subset) timed on it
-    worst_rel, checked = 0.0, 0
-    oracle_terms, oracle_s = 0.0, 0.0
+    ms, clocks = _clocked(timed)
+    t = ms / 1e3
+    _close(plans, graph)
+    # 4) oracle check, one matrix of every (ensemble, n) (the first of its group)
+    worst_rel, checked, oracle_terms, oracle_s = 0.0, 0, 0.0, 0.0
+    samples = []
     for cplx, (flat, ns, offs, out) in fields.items():
         got = out.cpu().numpy()
-        host = flat.cpu().numpy()
-        for g in range(len(ns) // count):
-            i = g * count
+        for gi in range(len(ns) // count):
+            i = gi * count
             n = int(ns[i])
-            if n > 16:
-                continue
-            A = host[offs[i]:offs[i] + n * n].reshape(n, n)
-            ref = O.perm_dp(A)
+            A = flat[offs[i]:offs[i] + n * n].cpu().numpy().reshape(n, n)
             t_o = time.perf_counter()
-            _, abs_terms = O.perm_ryser(A, with_abs=True)
+            ref = O.perm_dp(A)
             oracle_s += time.perf_counter() - t_o
             oracle_terms += n * 2.0 ** n
             err = abs(got[i] - ref)
-            assert err <= max(1e-9 * abs(ref), 64 * n * 2.0 ** -53 * abs_terms), (cplx, n, got[i], ref)
+            if err > 1e-9 * abs(ref):
+                _, abs_terms = O.perm_ryser(A, with_abs=True)
+                assert err <= 64 * n * 2.0 ** -53 * abs_terms, (cplx, n, got[i], ref)
             worst_rel = max(worst_rel, err / abs(ref))
             checked += 1
-    oracle_rate = oracle_terms / max(oracle_s, 1e-9)
-    # the paper's CPU algorithm on one core (plain double Gray walk): one matrix
-    # of each field at every size, extrapolated to the step by n 2^n terms
+            samples.append(A)
+    del fields
+    # 5) per size: batched (scale/10, own graph) against one call per matrix
+    per_size = []
+    sub = max(2, count // 10)
+    for n in SIZES:
+        row = {"n": n}
+        part = {}
+        for cplx, names in ((True, CPLX), (False, REAL)):
+            from workloads import device as D
+            mats = [D.batch(name, n, sub, seed=5000 + 1000 * ei + n + (0 if cplx else 500))
+                    for ei, name in enumerate(names)]
+            flat = torch.cat([m.reshape(-1) for m in mats])
+            ns = np.full(sub * len(names), n, np.int32)
+            offs = np.arange(len(ns), dtype=np.int64) * n * n
+            out = torch.empty(len(ns), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+            part[cplx] = (flat, ns, offs, out)
+        pl, g = _graph_for(px, part)
+        g.launch(stream)
+        torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record(stream)
+        g.launch(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_b = a.elapsed_time(b)
+        _close(pl, g)
+        perms = sum(len(v[1]) for v in part.values())
+        row["batched_perms_per_s"] = perms / ms_b * 1e3
+        row["batched_matrices"] = perms
+        # plain: one call per matrix, 8 of every (ensemble, n)
+        plain_ms, plain_perms = 0.0, 0
+        for cplx, (flat, ns, offs, out) in part.items():
+            fn = px.perm_c128 if cplx else px.perm_f64
+            idx = [e * sub + k for e in range(3) for k in range(8)]
+            fn(flat, ns[:1], offs[:1], out[:1], stream)
+            torch.cuda.synchronize()
+            a, b = _events(torch)
+            a.record(stream)
+            for i in idx:
+                fn(flat, ns[i:i + 1], offs[i:i + 1], out[i:i + 1], stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            plain_ms += a.elapsed_time(b)
+            plain_perms += len(idx)
+        row["plain_perms_per_s"] = plain_perms / plain_ms * 1e3
+        row["plain_matrices"] = plain_perms
+        row["batched_over_plain"] = row["batched_perms_per_s"] / row["plain_perms_per_s"]
+        per_size.append(row)
+        del part
+    # restore the built-in chunking for whatever runs next in this process
+    for field in fields_keys.values():
+        for n in SIZES:
+            px.perm_tune_set(field, n, 0)
+    # the paper's CPU algorithm on one core (plain double Gray walk) over the checked matrices
     from oracle import cpu_walk as W
     walk_terms, walk_s = 0.0, 0.0
-    for cplx, (flat, ns, offs, out) in fields.items():
-        host = flat.cpu().numpy()
-        for g in range(len(ns) // count):
-            i = g * count
-            n = int(ns[i])
-            A = host[offs[i]:offs[i] + n * n].reshape(n, n)
-            t_w = time.perf_counter()
-            W.perm(A)
-            walk_s += time.perf_counter() - t_w
-            walk_terms += n * 2.0 ** n
+    for A in samples:
+        t_w = time.perf_counter()
+        W.perm(A)
+        walk_s += time.perf_counter() - t_w
+        walk_terms += A.shape[0] * 2.0 ** A.shape[0]
+    oracle_rate = oracle_terms / max(oracle_s, 1e-9)
     walk_rate = walk_terms / max(walk_s, 1e-9)
-    line = {"workload": "ensembles_batched", "metric": "perms_per_s", "value": total_perms / t, "unit": "perm/s",
-            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
-            "nominal_terms_per_s": total_terms / t, "perms_per_step": total_perms,
-            "plain_perms_per_s": plain_perms / (plain_ms / 1e3),
-            "plain_nominal_terms_per_s": plain_terms / (plain_ms / 1e3),
-            "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel,
+    plain_all = sum(r["plain_matrices"] for r in per_size) / sum(
+        r["plain_matrices"] / r["plain_perms_per_s"] for r in per_size)
+    return {"metric": "perms_per_s", "value": total_perms / t, "unit": "perm/s", "higher_is_better": True,
+            "ms_per_step": ms, "steps": 1, "perms_per_step": total_perms,
+            "nominal_terms_per_s": total_terms / t, "evaluated_terms_per_s": eval_terms / t,
+            "plain_perms_per_s_same_mix": _mix_rate(per_size, count),
+            "plain_perms_per_s_sampled": plain_all,
+            "per_size": per_size, "tuned_chunk_log2": table, "tune_file": tune_path, "tune_s": tune_s,
+            "generate_s": gen_s, "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel,
+            "launch": "one CUDA graph (perm_graph_*) of two plans, every (field, n) walk a parallel branch",
+            "clocks": clocks, "dtype": "c128+f64",
+            "data": "synthetic, generated on the device (seeded torch generators)",
             "cpu_baseline": {"value": oracle_rate, "unit": "terms/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"Ryser in double-double on the {checked} checked matrices (n <= 16), "
-                                       "n 2^n terms each",
+                             "sample": f"perm_dp (double-double row-expansion DP) on the {checked} checked "
+                                       "matrices, n 2^n terms each",
                              "extrapolated_s_per_step": total_terms / oracle_rate,
                              "gray_walk_single_core": {
                                  "value": walk_rate, "unit": "terms/s", "cores": 1,
                                  "kind": "plain CPU Gray-code walk (uncompensated double / complex double)",
-                                 "sample": f"the first matrix of every (ensemble, n) group, {walk_s:.1f} s",
+                                 "sample": f"the {checked} checked matrices, {walk_s:.1f} s",
                                  "extrapolated_s_per_step": total_terms / walk_rate}},
-            "dtype": "c128+f64",
-            "data": "synthetic, generated on the device (seeded torch generators)",
-            "config": {"sizes": list(SIZES), "per_size_and_ensemble": count, "scale_of_50000": args.scale,
-                       "complex128": list(CPLX), "float64": list(REAL)}}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": "ensembles_ragged_6x5x50000", "sizes": list(SIZES),
+                       "per_size_and_ensemble": count, "scale_of_50000": scale,
+                       "complex128": list(CPLX), "float64": list(REAL),
+                       "warmup": "one replay of a graph of the same kernels on 1/1000 of the batch",
+                       "l2": f"inputs {input_bytes / 2 ** 30:.2f} GiB, read once per step (larger than L2)"}}
+
+
+def _mix_rate(per_size, count):
+    """Plain (one call per matrix) perms/s of the whole batch, from the per-size
+    plain rates weighted by the batch's composition (6 x count at every n)."""
+    secs = sum(6 * count / r["plain_perms_per_s"] for r in per_size)
+    return 6 * count * len(per_size) / secs
+
+
+def ensembles_batched(args):
+    d = batched_object(args.scale)
+    d["workload"] = "ensembles_batched"
+    print(json.dumps(d), flush=True)
     return 0
 
 
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
-
-class _Server:
-    def __init__(self, px, plain: int, device_bytes: int = 4 << 30):
-        self.px, self.lib = px, px._lib
-        L = self.lib
-        L.serve_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
-        L.serve_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint32,
-                                   ctypes.POINTER(ctypes.c_uint64)]
-        L.serve_poll_timed.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
-                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
-                                       ctypes.POINTER(ctypes.c_int64)]
-        L.serve_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
-        L.serve_destroy.argtypes = [ctypes.c_void_p]
-        buf = bytearray(32)
-        struct.pack_into("<iiqqii", buf, 0, 1 << 20, 8192, device_bytes, 0, 0, plain)
-        self._cfg = (ctypes.c_char * 32).from_buffer(buf)
-        self.h = ctypes.c_void_p()
-        rc = L.serve_create(ctypes.addressof(self._cfg), ctypes.byref(self.h))
-        if rc:
-            raise RuntimeError(px.last_error())
-        self.res = (ctypes.c_char * 16)()
-        self.done, self.ts, self.td = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
-
-    def submit(self, A, field, p):
-        t = ctypes.c_uint64()
-        rc = self.lib.serve_submit(self.h, field, A.shape[0], A.ctypes.data, p, ctypes.byref(t))
-        if rc:
-            raise RuntimeError(self.px.last_error())
-        return t.value
-
-    def poll(self, ticket):
-        rc = self.lib.serve_poll_timed(self.h, ticket, self.res, ctypes.byref(self.done), ctypes.byref(self.ts),
-                                       ctypes.byref(self.td))
-        if rc:
-            raise RuntimeError(self.px.last_error())
-        if not self.done.value:
-            return None
-        return (self.td.value - self.ts.value) * 1e-9, bytes(self.res)
-
-    def stats(self):
-        s = (ctypes.c_int64 * 5)()
-        self.lib.serve_stats(self.h, s)
-        return list(s)
-
-    def close(self):
-        self.lib.serve_destroy(self.h)
-
 
 def _request_mix(count: int, seed: int):
     import oracle as O   # primes for the F_p requests (largest p = 1 mod n below 2^31)
@@ -545,9 +626,11 @@ def _request_mix(count: int, seed: int):
 
 
 def _drive(S, reqs, arrivals):
-    """Submit at the given arrival times (s), poll until all done; returns latencies and makespan."""
+    """Submit at the given arrival times (s), poll until all done; returns
+    latencies (measured inside the library), makespan and results."""
     pending = {}
     lat = []
+    results = [None] * len(reqs)
     t0 = time.perf_counter()
     i = 0
     while i < len(reqs) or pending:
@@ -559,50 +642,83 @@ def _drive(S, reqs, arrivals):
         for tk in list(pending):
             r = S.poll(tk)
             if r is not None:
-                lat.append(r[0])
+                results[pending[tk]] = r[0]
+                lat.append(r[1])
                 del pending[tk]
         if i < len(reqs) and not pending:
             time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.001)))
-    return lat, time.perf_counter() - t0
+    return lat, time.perf_counter() - t0, results
+
+
+def served_object(scale: float = 1.0) -> dict:
+    """Config 4: a Poisson stream of 20,000 requests (x scale) at 70 % of the
+    measured capacity, mixing complex128 Haar n ~ U[10,26], float64 GOE
+    n ~ U[10,26], complex128 cycle-geodesic points (odd n in [9,25], t on the
+    201-point grid) and F_p random matrices n ~ U[16,30]; p50 / p99 latency
+    (submit -> completion, measured inside the library) and throughput for the
+    continuous-batching server and for the plain FIFO server (one batched call
+    per request) on the same trace, both saturated rates, and the GPU-busy
+    fraction (device time of the steps / makespan)."""
+    import paper_2602_10141_b300 as px
+    count = max(200, int(round(20000 * scale)))
+    t0 = time.perf_counter()
+    reqs = _request_mix(count, seed=0)
+    gen_s = time.perf_counter() - t0
+
+    def run_all():
+        # saturated: a calibration sample submitted at once, continuous and plain FIFO
+        cal = reqs[: max(100, count // 5)]
+        sat = {}
+        for name, plain in (("continuous", False), ("plain_fifo", True)):
+            S = px.Server(device_bytes=4 << 30, plain_fifo=plain)
+            _, span, _ = _drive(S, cal, [0.0] * len(cal))
+            st = S.stats()
+            S.close()
+            sat[name] = {"rps": len(cal) / span, "gpu_busy_frac": st["gpu_busy_ms"] / (span * 1e3)}
+        rate = 0.7 * sat["continuous"]["rps"]
+        g = np.random.default_rng(1)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
+        out, vals = {}, {}
+        for name, plain in (("continuous", False), ("plain_fifo", True)):
+            S = px.Server(device_bytes=4 << 30, plain_fifo=plain)
+            lat, span, res = _drive(S, reqs, arrivals)
+            st = S.stats()
+            S.close()
+            lat = np.array(lat)
+            out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                         "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                         "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+                         "throughput_rps": count / span, "makespan_s": span, "steps": st["steps"],
+                         "launches": st["launches"], "gpu_busy_ms": st["gpu_busy_ms"],
+                         "gpu_busy_frac": st["gpu_busy_ms"] / (span * 1e3)}
+            vals[name] = res
+        return sat, rate, out, vals
+
+    (sat, rate, out, vals), clocks = _clocked(run_all)
+    same = sum(1 for a, b in zip(vals["continuous"], vals["plain_fifo"]) if a == b or (a != a and b != b))
+    return {"metric": "p99_latency_ms", "value": out["continuous"]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "requests": count, "arrival_rate_rps": rate,
+            "capacity_rps": sat["continuous"]["rps"],
+            "saturated": {"continuous_rps": sat["continuous"]["rps"], "plain_fifo_rps": sat["plain_fifo"]["rps"],
+                          "continuous_over_plain": sat["continuous"]["rps"] / sat["plain_fifo"]["rps"],
+                          "continuous_gpu_busy_frac": sat["continuous"]["gpu_busy_frac"],
+                          "plain_fifo_gpu_busy_frac": sat["plain_fifo"]["gpu_busy_frac"],
+                          "requests": max(100, count // 5)},
+            "continuous": out["continuous"], "plain_fifo": out["plain_fifo"],
+            "results_bit_identical_continuous_vs_plain": f"{same}/{count}",
+            "clocks": clocks, "request_generation_s": gen_s,
+            "dtype": "c128+f64+u32", "data": "synthetic Poisson trace, seed 0",
+            "config": {"workload": "serving_poisson_mix_20000",
+                       "mix": "1/4 each: c128 Haar n~U[10,26], f64 GOE n~U[10,26], c128 cycle geodesic odd n in "
+                              "[9,25] t in k/200, F_p random n~U[16,30] with the largest p = 1 (mod n) < 2^31",
+                       "load": "0.7 x the continuous server's saturated rate", "scale_of_20000": scale,
+                       "work_budget": "automatic (2^33 complex128-term equivalents)"}}
 
 
 def serving(args):
-    import paper_2602_10141_b300 as px
-    count = max(200, int(round(20000 * args.scale)))
-    reqs = _request_mix(count, seed=0)
-    # capacity: all requests of a calibration sample submitted at once
-    cal = reqs[: max(100, count // 5)]
-    S = _Server(px, plain=0)
-    _, span = _drive(S, cal, [0.0] * len(cal))
-    S.close()
-    capacity = len(cal) / span
-    # the same sample through the plain FIFO server: its saturated throughput
-    S = _Server(px, plain=1)
-    _, span_plain = _drive(S, cal, [0.0] * len(cal))
-    S.close()
-    plain_capacity = len(cal) / span_plain
-    rate = 0.7 * capacity
-    g = np.random.default_rng(1)
-    arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
-    out = {}
-    for name, plain in (("continuous", 0), ("plain_fifo", 1)):
-        S = _Server(px, plain=plain)
-        lat, span = _drive(S, reqs, arrivals)
-        st = S.stats()
-        S.close()
-        lat = np.array(lat)
-        out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                     "throughput_rps": count / span, "makespan_s": span, "steps": st[3], "launches": st[4]}
-    line = {"workload": "serving", "metric": "p99_latency_ms", "value": out["continuous"]["p99_ms"], "unit": "ms",
-            "higher_is_better": False, "requests": count, "arrival_rate_rps": rate,
-            "capacity_rps": capacity, "saturated_rps": {"continuous": capacity, "plain_fifo": plain_capacity,
-                                                        "requests": len(cal)},
-            "continuous": out["continuous"], "plain_fifo": out["plain_fifo"],
-            "dtype": "c128+f64+u32", "data": "synthetic Poisson trace, seed 0",
-            "config": {"mix": "1/4 each: c128 Haar n~U[10,26], f64 GOE n~U[10,26], c128 cycle geodesic odd n in "
-                              "[9,25] t in k/200, F_p random n~U[16,30] with the largest p = 1 (mod n) < 2^31",
-                       "load": "0.7 x capacity", "scale_of_20000": args.scale}}
-    print(json.dumps(line), flush=True)
+    d = served_object(args.scale)
+    d["workload"] = "serving"
+    print(json.dumps(d), flush=True)
     return 0
 
 

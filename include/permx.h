@@ -137,8 +137,9 @@ int perm_modp_host(const uint32_t* A, const int32_t* n, const int64_t* offset, c
  * indices in [0, m), repeats allowed; checked before anything is enqueued
  * (EINVAL names the first bad index).  out: DEVICE array of batch values.
  * 1 <= n <= PERMX_MAX_N_FP, m >= 1 (n may exceed m when modes repeat).
- * Asynchronous on `stream` after the host checks (the index arrays are
- * copied during the call).  Each result has the bits perm_c128 / perm_f64
+ * Asynchronous on `stream` after the host checks, except that copying the
+ * index arrays waits for the work already on `stream` (they are copied during
+ * the call, so the caller may reuse them at once).  Each result has the bits perm_c128 / perm_f64
  * gives for the extracted n x n matrix.  Errors: EINVAL, ENOMEM, ECUDA. */
 int perm_c128_gather(const perm_c128_t* U, int32_t m, int64_t ldu, const int32_t* rows, const int32_t* cols,
                      int32_t n, int64_t batch, perm_c128_t* out, void* stream);
@@ -183,8 +184,13 @@ int perm_modp_gray_range(const uint32_t* A, int32_t n, uint32_t p, uint64_t k0, 
  * memset on `stream` (A, out: device buffers laid out as planned), so it may
  * be captured in a CUDA graph; perm_plan_graph_launch does that capture
  * itself on first use for a given (A, out) pair and afterwards replays the
- * graph with one launch.  Executions of one plan must not overlap on the
- * GPU (they share the workspace).  Errors: EINVAL, ENOMEM, ECUDA.
+ * graph with one launch.  The Gray walks of the plan's size groups run
+ * concurrently on streams the plan owns (forked from and joined back into
+ * `stream`; in a capture, parallel branches of the graph), largest walk
+ * first, so small sizes fill the tail of large ones; one-shot batched calls
+ * do the same on streams of the calling thread.  Executions of one plan must
+ * not overlap on the GPU (they share the workspace).  Errors: EINVAL, ENOMEM,
+ * ECUDA.
  * ---------------------------------------------------------------------- */
 typedef struct perm_plan perm_plan;
 int perm_plan_create(int field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
@@ -192,6 +198,23 @@ int perm_plan_create(int field, const int32_t* n, const int64_t* offset, const u
 int perm_plan_execute(perm_plan* plan, const void* A, void* out, void* stream);
 int perm_plan_graph_launch(perm_plan* plan, const void* A, void* out, void* stream);
 int perm_plan_destroy(perm_plan* plan);
+
+/* Several plans (e.g. a complex128 and a float64 batch of paper §3-§7
+ * ensembles) captured into ONE CUDA graph: plans[i] runs on A[i] -> out[i]
+ * (device buffers laid out as that plan was created), each plan a parallel
+ * branch of the graph and each of its size groups a branch of that, so one
+ * perm_graph_launch (asynchronous on `stream`) computes every plan's batch
+ * with the smaller walks overlapping the larger ones.  Results are
+ * bit-identical to perm_plan_execute of each plan.  All plans must belong to
+ * the current device, appear once, and not execute elsewhere while a launch
+ * of the graph runs (they share their workspaces with it).  count >= 1.
+ * perm_graph_create captures on a private stream and synchronises nothing;
+ * perm_graph_destroy synchronises the device.  Errors: EINVAL, ECUDA. */
+typedef struct perm_graph perm_graph;
+int perm_graph_create(perm_plan* const* plans, const void* const* A, void* const* out, int32_t count,
+                      perm_graph** graph);
+int perm_graph_launch(perm_graph* graph, void* stream);
+int perm_graph_destroy(perm_graph* graph);
 
 /* Chunk-length tuning (paper §2.2: the size of a Gray-code block).  The
  * chunk length of a float matrix is 2^ell Gray steps with ell a function of
@@ -288,9 +311,20 @@ int perm_schur_prime_count(int32_t n);
  * arriving as a stream).  A server owns a CUDA stream, device slots for
  * matrices and partial sums, and a host queue.  serve_submit copies the
  * matrix and returns a ticket at once; admitted requests are advanced by
- * bounded steps (a fixed budget of Gray-code chunks per step), new arrivals
- * join at the next step, and a request completes when all its chunks are
- * summed.  Each result equals the batched-path result for the same matrix.
+ * bounded steps (per (field, n) class one wave of Gray-code chunks per step),
+ * new arrivals join at the next step, and a request completes when all its
+ * chunks are summed.  Each result equals the batched-path result for the same
+ * matrix.  Admission takes queued requests in arrival order while three
+ * limits allow: the number of resident requests, device memory (a first-fit
+ * arena of device_bytes) and outstanding work.  The work of a request is its
+ * n 2^(n-1) Gray-walk terms weighted by the cost of its field's term on the
+ * GPU (complex128 = 1; float64 = 0.32 and F_p = 0.1 in integer-mantissa mode,
+ * complex128 = 3.4 and float64 = 1.4 in FP64 mode), counted until the steps
+ * that run its chunks have completed.  A request whose work does not fit lets smaller
+ * ones behind it pass, for at most 20 ms; after that nothing passes it until
+ * it fits (or nothing else is resident).  Two steps are in flight: the
+ * worker plans and enqueues step k+1 while step k runs on the GPU, and reads
+ * a step's results once that step has completed.
  * Thread-safe: submit and poll may be called from different threads.
  * ---------------------------------------------------------------------- */
 #define PERMX_FIELD_C128 0
@@ -304,7 +338,18 @@ typedef struct {
     int64_t chunks_per_step;     /* Gray-code chunks advanced per step (0 = automatic) */
     int32_t device;              /* CUDA device ordinal */
     int32_t plain_fifo;          /* 1 = baseline: one request at a time, one launch per request */
+    int64_t work_budget;         /* outstanding work admitted at once, in complex128-term equivalents
+                                    (0 = automatic, 2^33, about 30 ms of the GPU; < 0 = no limit) */
 } perm_serve_cfg;
+
+/* Counters of a server (serve_stats2). */
+typedef struct {
+    int64_t submitted, completed, resident, steps, launches;
+    int64_t pending;             /* queued, not yet admitted */
+    int64_t resident_work;       /* admitted work not yet run by a completed step (units of work_budget) */
+    double gpu_busy_ms;          /* sum over steps of the device time from a step's first to its last operation */
+    double uptime_ms;            /* host time since serve_create */
+} perm_serve_stats;
 
 typedef struct perm_server perm_server;
 
@@ -323,6 +368,9 @@ int serve_poll_timed(perm_server* h, uint64_t ticket, void* result, int* done, i
 int serve_drain(perm_server* h, int64_t timeout_ms);
 /* Counters: submitted, completed, resident, steps, launches (host array of 5). */
 int serve_stats(perm_server* h, int64_t* stats5);
+/* All counters, including the GPU-busy time (gpu_busy_ms / uptime_ms is the
+ * fraction of the server's life the GPU spent on its steps). */
+int serve_stats2(perm_server* h, perm_serve_stats* out);
 int serve_destroy(perm_server* h);
 
 /* ------------------------------------------------------------------------

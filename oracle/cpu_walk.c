@@ -62,30 +62,35 @@ int cpuwalk_modp_gray_range(int n, const uint32_t* A, uint32_t p, uint64_t k0, u
     return 0;
 }
 
-/* The same sum with the range cut into one contiguous block per OpenMP
- * thread; the block sums are added mod p in block order.  Returns the number
- * of threads used (>= 1) or -1. */
+/* The same sum with the range cut into nb = omp_get_max_threads() contiguous
+ * blocks, shared out by an OpenMP loop (so every block is walked however many
+ * threads the runtime grants); the block sums are added mod p in block order.
+ * Returns the number of threads that ran (>= 1) or -1. */
 int cpuwalk_modp_gray_range_mt(int n, const uint32_t* A, uint32_t p, uint64_t k0, uint64_t k1, uint32_t* out) {
     if (n < 1 || n > 63 || !A || !out || p < 2 || k0 > k1 || k1 > (1ull << n)) return -1;
-    const int nt = omp_get_max_threads();
-    uint32_t* part = (uint32_t*)calloc((size_t)nt, sizeof(uint32_t));
+    const int nb = omp_get_max_threads();
+    uint32_t* part = (uint32_t*)calloc((size_t)nb, sizeof(uint32_t));
     if (!part) return -1;
     const uint64_t len = k1 - k0;
-    int rc = 0;
-    #pragma omp parallel num_threads(nt) reduction(|:rc)
+    const uint64_t q = len / (uint64_t)nb, r = len % (uint64_t)nb;   // the first r blocks get one more
+    int rc = 0, used = 1;
+    #pragma omp parallel reduction(|:rc)
     {
-        const int t = omp_get_thread_num();
-        const uint64_t q = len / (uint64_t)nt, r = len % (uint64_t)nt;   // the first r blocks get one more
-        const uint64_t a = k0 + q * (uint64_t)t + ((uint64_t)t < r ? (uint64_t)t : r);
-        const uint64_t b = a + q + ((uint64_t)t < r ? 1 : 0);
-        rc |= cpuwalk_modp_gray_range(n, A, p, a, b, &part[t]) != 0;
+        #pragma omp single
+        used = omp_get_num_threads();
+        #pragma omp for schedule(static, 1)
+        for (int t = 0; t < nb; ++t) {
+            const uint64_t a = k0 + q * (uint64_t)t + ((uint64_t)t < r ? (uint64_t)t : r);
+            const uint64_t b = a + q + ((uint64_t)t < r ? 1 : 0);
+            rc |= cpuwalk_modp_gray_range(n, A, p, a, b, &part[t]) != 0;
+        }
     }
     uint64_t s = 0;
-    for (int t = 0; t < nt; ++t) s = (s + part[t]) % p;
+    for (int t = 0; t < nb; ++t) s = (s + part[t]) % p;
     free(part);
     if (rc) return -1;
     *out = (uint32_t)s;
-    return nt;
+    return used;
 }
 
 /* The same signed sum over real entries in plain double (no (-1)^n factor). */

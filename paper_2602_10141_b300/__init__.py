@@ -84,6 +84,17 @@ def _load() -> ctypes.CDLL:
         "perm_sample_stats": ([ctypes.c_int, vp, i64, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         "permx_peak_probe": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                               P(ctypes.c_double)], ctypes.c_int),
+        "perm_graph_create": ([P(vp), P(vp), P(vp), i32, P(vp)], ctypes.c_int),
+        "perm_graph_launch": ([vp, vp], ctypes.c_int),
+        "perm_graph_destroy": ([vp], ctypes.c_int),
+        "serve_create": ([vp, P(vp)], ctypes.c_int),
+        "serve_submit": ([vp, ctypes.c_int, i32, vp, u32, P(u64)], ctypes.c_int),
+        "serve_poll": ([vp, u64, vp, P(ctypes.c_int)], ctypes.c_int),
+        "serve_poll_timed": ([vp, u64, vp, P(ctypes.c_int), P(i64), P(i64)], ctypes.c_int),
+        "serve_drain": ([vp, i64], ctypes.c_int),
+        "serve_stats": ([vp, P(i64)], ctypes.c_int),
+        "serve_stats2": ([vp, vp], ctypes.c_int),
+        "serve_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -121,12 +132,24 @@ def _p(a: np.ndarray, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+def _current_device() -> int:
+    """Index of the calling thread's current CUDA device (the library launches there)."""
+    import torch
+    return torch.cuda.current_device()
+
+
 def _stream(stream) -> int | None:
+    """Raw cudaStream_t of `stream` (None: torch's current stream; an int is
+    taken as a raw handle).  A torch stream must belong to the current device."""
     if stream is None:
         import torch
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, int):
         return stream
+    dev = getattr(stream, "device", None)
+    idx = getattr(dev, "index", None)
+    if idx is not None and idx != _current_device():
+        raise ValueError(f"the stream is on cuda:{idx}, the current device is cuda:{_current_device()}")
     return stream.cuda_stream
 
 
@@ -174,9 +197,22 @@ def _tensors(*specs) -> None:
             raise ValueError(f"{what} must be contiguous")
         if t.numel() < need:
             raise ValueError(f"{what} holds {t.numel()} elements; the call needs {need}")
-    for t, what, _, _ in specs:
+    _on_current_device(*[(t, what) for t, what, _, _ in specs])
+
+
+def _on_current_device(*named) -> None:
+    """Every (tensor, name) must be a CUDA tensor on the current device: the
+    library launches on the current device and would otherwise be handed
+    another GPU's pointers."""
+    for t, what in named:
         if not t.is_cuda:
             raise ValueError(f"{what} must be on a CUDA device")
+    cur = _current_device()
+    for t, what in named:
+        idx = t.device.index
+        if idx != cur:
+            raise ValueError(f"{what} is on cuda:{idx}, the current device is cuda:{cur}; "
+                             "all tensors of a call must be on the current device")
 
 
 # ---------------------------------------------------------------------------
@@ -223,8 +259,7 @@ def perm_gather(U, rows, cols, out, stream=None):
     if U.dtype not in (torch.complex128, torch.float64):
         raise TypeError("U must be complex128 or float64")
     _tensors((out, "out", "c128" if U.dtype == torch.complex128 else "f64", rows.shape[0]))
-    if not U.is_cuda:
-        raise ValueError("U must be on a CUDA device")
+    _on_current_device((U, "U"), (out, "out"))
     _check(f(U.data_ptr(), U.shape[0], U.stride(0), _p(rows, ctypes.c_int32), _p(cols, ctypes.c_int32),
              rows.shape[1], rows.shape[0], out.data_ptr(), _stream(stream)))
     return out
@@ -246,8 +281,7 @@ def _values_field(values) -> int:
         raise TypeError("values must be complex128 or float64")
     if not values.is_contiguous():
         raise ValueError("values must be contiguous")
-    if not values.is_cuda:
-        raise ValueError("values must be on a CUDA device")
+    _on_current_device((values, "values"))
     return field
 
 
@@ -282,8 +316,9 @@ def perm_sample_stats_async(values, out, threshold: float = float("inf"), real_t
     field = _values_field(values)
     if out.numel() * out.element_size() < ctypes.sizeof(PermStats):
         raise ValueError("output buffer too small for perm_stats_t")
-    if not out.is_cuda or not out.is_contiguous():
+    if not out.is_contiguous():
         raise ValueError("out must be a contiguous CUDA tensor")
+    _on_current_device((values, "values"), (out, "out"))
     _check(_lib.perm_sample_stats(field, values.data_ptr(), values.numel(), threshold, real_tol,
                                   out.data_ptr(), _stream(stream)))
     return out
@@ -293,6 +328,7 @@ def perm_sample_stats(values, threshold: float = float("inf"), real_tol: float =
     """Statistics of the device tensor `values` (see perm_sample_stats in permx.h), as a dict.
     Synchronises the stream."""
     import torch
+    _values_field(values)                      # type, layout and device before anything is allocated
     out = torch.empty(ctypes.sizeof(PermStats), dtype=torch.uint8, device=values.device)
     perm_sample_stats_async(values, out, threshold, real_tol, stream)
     torch.cuda.synchronize(values.device)
@@ -332,6 +368,126 @@ class Plan:
     def close(self):
         if self.h:
             _lib.perm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """Several plans captured into one CUDA graph (perm_graph_*): plans[i] runs
+    on A[i] -> out[i]; ``launch`` replays all of them with one graph launch."""
+
+    def __init__(self, plans, A, out):
+        if not (len(plans) == len(A) == len(out)) or not plans:
+            raise ValueError("need one A and one out per plan")
+        for pl, a, o in zip(plans, A, out):
+            pl._args(a, o)
+        n = len(plans)
+        self._keep = (list(plans), list(A), list(out))
+        hp = (ctypes.c_void_p * n)(*[pl.h.value for pl in plans])
+        ha = (ctypes.c_void_p * n)(*[a.data_ptr() for a in A])
+        ho = (ctypes.c_void_p * n)(*[o.data_ptr() for o in out])
+        h = ctypes.c_void_p()
+        _check(_lib.perm_graph_create(hp, ha, ho, n, ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(_lib.perm_graph_launch(self.h, _stream(stream)))
+
+    def close(self):
+        if self.h:
+            _lib.perm_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServeCfg(ctypes.Structure):
+    """perm_serve_cfg (include/permx.h): the serving loop's limits."""
+    _fields_ = [("max_requests", ctypes.c_int32), ("max_resident", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("chunks_per_step", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("plain_fifo", ctypes.c_int32),
+                ("work_budget", ctypes.c_int64)]
+
+
+class ServeStats(ctypes.Structure):
+    """perm_serve_stats (include/permx.h): counters of a server."""
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "resident", "steps", "launches",
+                                              "pending", "resident_work")] + \
+        [("gpu_busy_ms", ctypes.c_double), ("uptime_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_RESULT_BYTES = {FIELD_C128: 16, FIELD_F64: 8, FIELD_MODP: 4}
+
+
+class Server:
+    """Continuous-batching server (serve_*): ``submit`` copies a host matrix and
+    returns a ticket, ``poll`` returns None until the result is ready, then
+    (value, latency_s) with the latency measured inside the library."""
+
+    def __init__(self, max_requests: int = 0, max_resident: int = 0, device_bytes: int = 0,
+                 chunks_per_step: int = 0, device: int | None = None, plain_fifo: bool = False,
+                 work_budget: int = 0):
+        self.cfg = ServeCfg(max_requests, max_resident, device_bytes, chunks_per_step,
+                            _current_device() if device is None else device, int(bool(plain_fifo)), work_budget)
+        h = ctypes.c_void_p()
+        _check(_lib.serve_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+        self._res = (ctypes.c_char * 16)()
+        self._done = ctypes.c_int(0)
+        self._ts, self._td = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._field = {}
+
+    def submit(self, A: np.ndarray, field: int, p: int = 0) -> int:
+        """A: square host matrix (complex128, float64 or uint32 residues < p)."""
+        dt = {FIELD_C128: np.complex128, FIELD_F64: np.float64, FIELD_MODP: np.uint32}.get(field)
+        if dt is None:
+            raise ValueError("unknown field")
+        A = np.ascontiguousarray(A, dtype=dt)
+        if A.ndim != 2 or A.shape[0] != A.shape[1]:
+            raise ValueError("A must be a square matrix")
+        t = ctypes.c_uint64()
+        _check(_lib.serve_submit(self.h, field, A.shape[0], A.ctypes.data, p, ctypes.byref(t)))
+        self._field[t.value] = field
+        return t.value
+
+    def poll(self, ticket: int):
+        _check(_lib.serve_poll_timed(self.h, ticket, self._res, ctypes.byref(self._done), ctypes.byref(self._ts),
+                                     ctypes.byref(self._td)))
+        if not self._done.value:
+            return None
+        field = self._field.pop(ticket)
+        raw = bytes(self._res)[:_RESULT_BYTES[field]]
+        if field == FIELD_C128:
+            v = complex(*np.frombuffer(raw, np.float64))
+        elif field == FIELD_F64:
+            v = float(np.frombuffer(raw, np.float64)[0])
+        else:
+            v = int(np.frombuffer(raw, np.uint32)[0])
+        return v, (self._td.value - self._ts.value) * 1e-9
+
+    def drain(self, timeout_ms: int = 60000) -> None:
+        _check(_lib.serve_drain(self.h, timeout_ms))
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(_lib.serve_stats2(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            _lib.serve_destroy(self.h)
             self.h = None
 
     def __del__(self):

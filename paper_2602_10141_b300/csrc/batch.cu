@@ -8,6 +8,7 @@
 // the batch: the chunking is a function of (n, field) only and chunk partials
 // are combined in a fixed order.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -50,15 +51,17 @@ int chunk_log2(Field field, int n, int bits) {
 int chunk_log2_fp(int bits) {
     // About 2^14 chunks per matrix (2^(bits-3) for small walks) so that even
     // one matrix spreads over many threads (a chunk's steps run serially, so
-    // its length sets the latency of a lone matrix); at most 2^10 steps per
-    // chunk (the float64 walk's row-sum drift grows like sqrt(L) ulps, and a
-    // chunk is the unit of work a serving step cannot split); at least 2^3
-    // steps (or the whole walk), where the O(n^2) chunk start is still small
-    // next to the n products per step.
+    // its length sets the latency of a lone matrix); at most 2^8 steps per
+    // chunk (a chunk is the unit of work a serving step cannot split: 2^8
+    // steps of a complex n = 26 walk take about 2 ms on one thread, and the
+    // float64 walk's row-sum drift grows like sqrt(L) ulps), which costs
+    // n^2 / (2^8 n) < 13 % extra row-sum work at n = 32; at least 2^3 steps
+    // (or the whole walk), where the O(n^2) chunk start is still small next to
+    // the n products per step.
     int ell = bits - 14;
     int lo = bits < 3 ? bits : 3;
     if (ell < lo) ell = lo;
-    if (ell > 10) ell = 10;
+    if (ell > 8) ell = 8;
     return ell;
 }
 
@@ -619,6 +622,95 @@ void release_batch(Prepared& X, cudaStream_t s) {
     X.ws = nullptr;
 }
 
+cudaError_t StreamSet::create(int dev) {
+    device = dev;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int q = 0; q < kGroupStreams && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&side[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) destroy();
+    return e;
+}
+
+void StreamSet::destroy() {
+    for (int q = 0; q < kGroupStreams; ++q) {
+        if (side[q]) cudaStreamDestroy(side[q]);
+        if (join[q]) cudaEventDestroy(join[q]);
+        side[q] = nullptr;
+        join[q] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+}
+
+namespace {
+// one stream set per device for the lifetime of the calling thread
+struct ThreadStreams {
+    StreamSet sets[64];
+    bool failed[64] = {};
+    ~ThreadStreams() {
+        for (auto& x : sets)
+            if (x.fork) x.destroy();
+    }
+};
+}  // namespace
+
+StreamSet* thread_streams() {
+    static thread_local ThreadStreams T;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || T.failed[dev]) return nullptr;
+    StreamSet& x = T.sets[dev];
+    if (!x.fork && x.create(dev) != cudaSuccess) {
+        T.failed[dev] = true;
+        cudaGetLastError();
+        return nullptr;
+    }
+    return &x;
+}
+
+namespace {
+
+// Launch the walk of every size group, concurrently when there are several:
+// each group waits for the staging on `s` (fork event), runs on a stream of
+// the set, and `s` waits for all of them before the finalisation (join
+// events).  Under stream capture the same calls record a graph with one
+// parallel branch per group.
+template <typename LaunchGroup>
+cudaError_t launch_groups(const Prepared& X, cudaStream_t s, LaunchGroup&& launch) {
+    const size_t ng = X.P.groups.size();
+    StreamSet* ss = ng > 1 ? (X.streams ? X.streams : thread_streams()) : nullptr;
+    if (!ss) {
+        for (size_t gi = 0; gi < ng; ++gi) {
+            const cudaError_t e = launch(X.P.groups[gi], s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventRecord(ss->fork, s);
+    const int used = (int)std::min<size_t>(ng, kGroupStreams);
+    for (int q = 0; q < used && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(ss->side[q], ss->fork, 0);
+    // the largest walk first, so that the smaller groups fill its tail
+    std::vector<size_t> order(ng);
+    for (size_t gi = 0; gi < ng; ++gi) order[gi] = gi;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const GroupPlan &ga = X.P.groups[a], &gb = X.P.groups[b];
+        return (double)ga.mats.size() * ga.n * std::ldexp(1.0, ga.n) >
+               (double)gb.mats.size() * gb.n * std::ldexp(1.0, gb.n);
+    });
+    for (size_t k = 0; k < ng && e == cudaSuccess; ++k) e = launch(X.P.groups[order[k]], ss->side[k % kGroupStreams]);
+    // join every stream that waited on the fork, even after a failed launch, so
+    // that no side stream is left part of a capture
+    for (int q = 0; q < used; ++q) {
+        cudaError_t f = cudaEventRecord(ss->join[q], ss->side[q]);
+        if (f == cudaSuccess) f = cudaStreamWaitEvent(s, ss->join[q], 0);
+        if (e == cudaSuccess) e = f;
+    }
+    return e;
+}
+
+}  // namespace
+
 int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
     unsigned char* d = X.ws;
     const int64_t batch = X.batch;
@@ -631,23 +723,23 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
                 reinterpret_cast<uint32_t*>(d + X.o_col));
             e = cudaGetLastError();
         }
-        for (size_t gi = 0; e == cudaSuccess && gi < X.P.groups.size(); ++gi) {
-            const GroupPlan& g = X.P.groups[gi];
-            ModpLaunch L;
-            L.colT = reinterpret_cast<const uint32_t*>(d + X.o_col) + g.col_off;
-            L.p = reinterpret_cast<const uint32_t*>(d + X.o_p) + g.first_mat;
-            L.pinv = reinterpret_cast<const uint32_t*>(d + X.o_pinv) + g.first_mat;
-            L.acc = reinterpret_cast<unsigned long long*>(d + X.o_acc) + g.first_mat;
-            L.mat_stride = g.mat_stride;
-            L.item_begin = 0;
-            L.item_end = (uint64_t)g.items;
-            L.k_lo = 0;
-            L.k_hi = (uint64_t)1 << walk_bits(g.n, g.nw);
-            L.ell = g.ell;
-            L.log2_chunks = g.log2_chunks;
-            L.nw = g.nw;
-            e = dispatch_modp(g.n, L, s);
-        }
+        if (e == cudaSuccess)
+            e = launch_groups(X, s, [&](const GroupPlan& g, cudaStream_t ls) {
+                ModpLaunch L;
+                L.colT = reinterpret_cast<const uint32_t*>(d + X.o_col) + g.col_off;
+                L.p = reinterpret_cast<const uint32_t*>(d + X.o_p) + g.first_mat;
+                L.pinv = reinterpret_cast<const uint32_t*>(d + X.o_pinv) + g.first_mat;
+                L.acc = reinterpret_cast<unsigned long long*>(d + X.o_acc) + g.first_mat;
+                L.mat_stride = g.mat_stride;
+                L.item_begin = 0;
+                L.item_end = (uint64_t)g.items;
+                L.k_lo = 0;
+                L.k_hi = (uint64_t)1 << walk_bits(g.n, g.nw);
+                L.ell = g.ell;
+                L.log2_chunks = g.log2_chunks;
+                L.nw = g.nw;
+                return dispatch_modp(g.n, L, ls);
+            });
         if (e == cudaSuccess) {
             finalize_modp_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
                 reinterpret_cast<const unsigned long long*>(d + X.o_acc), reinterpret_cast<const ModpFinal*>(d + X.o_fin),
@@ -676,20 +768,20 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
             Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<double*>(d + X.o_col));
     }
     e = cudaGetLastError();
-    for (size_t gi = 0; e == cudaSuccess && gi < X.P.groups.size(); ++gi) {
-        const GroupPlan& g = X.P.groups[gi];
-        FpLaunch L;
-        L.colT = reinterpret_cast<const double*>(d + X.o_col) + g.col_off;
-        L.partial = reinterpret_cast<double*>(d + X.o_part) + (size_t)pw * g.part_off;
-        L.mat_stride = g.mat_stride;
-        L.item_begin = 0;
-        L.item_end = (uint64_t)g.items;
-        L.ell = g.ell;
-        L.log2_chunks = g.log2_chunks;
-        L.nw = g.nw;
-        if (g.x64) e = cplx ? dispatch_x64c(g.n, L, s) : dispatch_x64r(g.n, L, s);
-        else e = cplx ? dispatch_c128(g.n, L, s) : dispatch_f64(g.n, L, s);
-    }
+    if (e == cudaSuccess)
+        e = launch_groups(X, s, [&](const GroupPlan& g, cudaStream_t ls) {
+            FpLaunch L;
+            L.colT = reinterpret_cast<const double*>(d + X.o_col) + g.col_off;
+            L.partial = reinterpret_cast<double*>(d + X.o_part) + (size_t)pw * g.part_off;
+            L.mat_stride = g.mat_stride;
+            L.item_begin = 0;
+            L.item_end = (uint64_t)g.items;
+            L.ell = g.ell;
+            L.log2_chunks = g.log2_chunks;
+            L.nw = g.nw;
+            if (g.x64) return cplx ? dispatch_x64c(g.n, L, ls) : dispatch_x64r(g.n, L, ls);
+            return cplx ? dispatch_c128(g.n, L, ls) : dispatch_f64(g.n, L, ls);
+        });
     if (e == cudaSuccess) {
         finalize_fp_kernel<<<(unsigned)batch, kFinalThreads, 0, s>>>(
             reinterpret_cast<const double*>(d + X.o_part), reinterpret_cast<const FpFinal*>(d + X.o_fin), cplx ? 1 : 0,

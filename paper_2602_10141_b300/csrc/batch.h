@@ -57,6 +57,23 @@ struct BatchPlan {
     std::vector<GroupPlan> groups;
 };
 
+// Streams on which the size groups of one batch run concurrently, so that
+// the tail of one group's Gray walk overlaps the next group's walk.  A set
+// belongs to one host thread (thread_streams) or to one plan, so two threads
+// never share a stream and a stream in a graph capture is never used by
+// another thread.  fork/join are reused by every execution of the set's owner.
+constexpr int kGroupStreams = 8;
+struct StreamSet {
+    int device = -1;
+    cudaStream_t side[kGroupStreams] = {};
+    cudaEvent_t fork = nullptr, join[kGroupStreams] = {};
+    cudaError_t create(int dev);   // on device dev (which must be current)
+    void destroy();
+};
+// This thread's stream set for the current device (created on first use), or
+// nullptr if it could not be created (the groups then run on the call's stream).
+StreamSet* thread_streams();
+
 struct Prepared {                   // a planned batch with its workspace (device) and metadata uploaded
     Field field = Field::MODP;
     int64_t batch = 0;
@@ -65,6 +82,7 @@ struct Prepared {                   // a planned batch with its workspace (devic
     unsigned char* ws = nullptr;
     size_t bytes = 0;
     size_t o_stage = 0, o_p = 0, o_pinv = 0, o_fin = 0, o_meta_end = 0, o_acc = 0, o_col = 0, o_part = 0;
+    StreamSet* streams = nullptr;   // group streams (nullptr: this thread's set)
 };
 int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
                   cudaStream_t s, Prepared& X);

@@ -54,11 +54,17 @@ int gather_run(const T* U, int32_t m, int64_t ldu, const int32_t* rows, const in
     int32_t* d_rows = static_cast<int32_t*>(ws);
     int32_t* d_cols = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(ws) + idx_bytes);
     T* d_sub = reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + 2 * idx_bytes);
-    cudaError_t e = cudaMemcpyAsync(d_rows, rows, sizeof(int32_t) * (size_t)idx, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cols, cols, sizeof(int32_t) * (size_t)idx, cudaMemcpyHostToDevice, s);
+    // the indices go through a private pageable copy: a copy from pageable memory
+    // has left the source by the time cudaMemcpyAsync returns (it waits for the
+    // stream's earlier work first), so the caller may reuse rows and cols, pinned
+    // or not, as soon as this call returns
+    const std::vector<int32_t> hrows(rows, rows + idx), hcols(cols, cols + idx);
+    cudaError_t e = cudaMemcpyAsync(d_rows, hrows.data(), sizeof(int32_t) * (size_t)idx, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cols, hcols.data(), sizeof(int32_t) * (size_t)idx, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        const int64_t want = (total + 255) / 256;
-        const int blocks = (int)(want < 148 * 16 ? (want < 1 ? 1 : want) : 148 * 16);
+        const int64_t want = (total + 255) / 256, cap = (int64_t)sm_count() * 16;
+        const int blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
         gather_kernel<T><<<blocks, 256, 0, s>>>(U, ldu, d_rows, d_cols, n, total, d_sub);
         e = cudaGetLastError();
     }

@@ -25,10 +25,22 @@ struct perm_plan {
     int device = 0;
     int field = 0;
     cudaStream_t capture = nullptr;
+    StreamSet streams;               // the size groups' streams (execute and capture)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* gA = nullptr;
     void* gOut = nullptr;
+};
+
+// Several plans captured into one CUDA graph: each plan's pass is a branch of
+// the graph (and each of its size groups a branch of that), so one launch runs
+// every plan's matrices concurrently.
+struct perm_graph {
+    int device = 0;
+    cudaStream_t capture = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -89,11 +101,14 @@ int perm_plan_create(int field, const int32_t* n, const int64_t* offset, const u
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = P->streams.create(P->device);
     if (e != cudaSuccess) {
         release_batch(P->X, s);
+        if (P->capture) cudaStreamDestroy(P->capture);
         delete P;
         return cuda_fail(e, "perm_plan_create");
     }
+    P->X.streams = &P->streams;
     *plan = P;
     return PERMX_OK;
 }
@@ -147,7 +162,86 @@ int perm_plan_destroy(perm_plan* P) {
     release_batch(P->X, P->capture);
     cudaStreamSynchronize(P->capture);
     cudaStreamDestroy(P->capture);
+    P->streams.destroy();
     delete P;
+    return PERMX_OK;
+}
+
+int perm_graph_create(perm_plan* const* plans, const void* const* A, void* const* out, int32_t count,
+                      perm_graph** graph) {
+    clear_error();
+    if (!graph || !plans || !A || !out || count < 1) return fail(PERMX_EINVAL, "bad arguments");
+    int dev = 0;
+    PERMX_CUDA(cudaGetDevice(&dev));
+    for (int32_t i = 0; i < count; ++i) {
+        if (!plans[i] || !A[i] || !out[i]) return fail(PERMX_EINVAL, "NULL plan or buffer");
+        if (plans[i]->device != dev) return fail(PERMX_EINVAL, "every plan must belong to the current device");
+        if (plans[i]->field == PERMX_FIELD_C128 &&
+            (reinterpret_cast<uintptr_t>(A[i]) % 16 || reinterpret_cast<uintptr_t>(out[i]) % 16))
+            return fail(PERMX_EINVAL, "complex128 arrays must be 16-byte aligned");
+        for (int32_t k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(PERMX_EINVAL, "a plan may appear only once in a graph");
+    }
+    perm_graph* G = new perm_graph();
+    G->device = dev;
+    cudaError_t e = cudaStreamCreateWithFlags(&G->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (G->capture) cudaStreamDestroy(G->capture);
+        delete G;
+        return cuda_fail(e, "perm_graph_create");
+    }
+    int rc = PERMX_OK;
+    e = cudaStreamBeginCapture(G->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // fork: every plan's pass starts on that plan's own capture stream
+        e = cudaEventRecord(G->fork, G->capture);
+        int32_t forked = 0;
+        for (; forked < count && e == cudaSuccess; ++forked)
+            e = cudaStreamWaitEvent(plans[forked]->capture, G->fork, 0);
+        for (int32_t i = 0; i < forked && e == cudaSuccess && rc == PERMX_OK; ++i)
+            rc = execute_batch(plans[i]->X, A[i], out[i], plans[i]->capture);
+        // join every forked stream back, whatever failed, so the capture can end
+        for (int32_t i = 0; i < forked; ++i) {
+            cudaError_t f = cudaEventRecord(plans[i]->streams.join[0], plans[i]->capture);
+            if (f == cudaSuccess) f = cudaStreamWaitEvent(G->capture, plans[i]->streams.join[0], 0);
+            if (e == cudaSuccess) e = f;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(G->capture, &g);
+        if (e == cudaSuccess) e = ec;
+        if (e == cudaSuccess && rc == PERMX_OK) e = cudaGraphInstantiate(&G->exec, g, 0);
+        if (e == cudaSuccess && rc == PERMX_OK) G->graph = g;
+        else if (g) cudaGraphDestroy(g);
+    }
+    if (rc == PERMX_OK && e != cudaSuccess) rc = cuda_fail(e, "perm_graph_create capture");
+    if (rc) {
+        cudaEventDestroy(G->fork);
+        cudaStreamDestroy(G->capture);
+        delete G;
+        return rc;
+    }
+    *graph = G;
+    return PERMX_OK;
+}
+
+int perm_graph_launch(perm_graph* G, void* stream) {
+    clear_error();
+    if (!G || !G->exec) return fail(PERMX_EINVAL, "NULL graph");
+    PERMX_CUDA(cudaGraphLaunch(G->exec, static_cast<cudaStream_t>(stream)));
+    return PERMX_OK;
+}
+
+int perm_graph_destroy(perm_graph* G) {
+    clear_error();
+    if (!G) return fail(PERMX_EINVAL, "NULL graph");
+    cudaSetDevice(G->device);
+    cudaDeviceSynchronize();
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    cudaEventDestroy(G->fork);
+    cudaStreamDestroy(G->capture);
+    delete G;
     return PERMX_OK;
 }
 

@@ -226,6 +226,18 @@ int schur_crt_run_primes(int n, const std::vector<uint32_t>& primes, const char*
 
     // Nijenhuis-Wilf form: 2^(n-1) Gray indices per prime
     const uint64_t total = 1ull << walk_bits(n, 1);
+    // a checkpoint whose checksum holds can still carry values no run writes:
+    // reject them before any GPU work (a cursor at or past the end would never
+    // advance, a residue at or above its prime would corrupt the CRT)
+    for (size_t i = 0; i < st.done.size(); ++i)
+        if (st.done[i] >= primes[i]) return fail(PERMX_EIO, "checkpoint " + path + ": residue not below its prime");
+    if (st.done.size() < primes.size()) {
+        if (st.cursor >= total) return fail(PERMX_EIO, "checkpoint " + path + ": cursor past the end of the walk");
+        if (st.partial >= primes[st.done.size()])
+            return fail(PERMX_EIO, "checkpoint " + path + ": partial sum not below its prime");
+    } else if (st.cursor != 0 || st.partial != 0) {
+        return fail(PERMX_EIO, "checkpoint " + path + ": finished run with a cursor");
+    }
     const int ell = chunk_log2_modp(walk_bits(n, 1));
     uint64_t slice = slice_subsets ? slice_subsets : (n <= 38 ? total : (1ull << 37));
     const uint64_t Lc = 1ull << ell;

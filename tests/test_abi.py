@@ -227,3 +227,51 @@ def test_binding_rejects_tensors_that_do_not_fit(px):
         px.perm_sample_stats(torch.zeros(4, dtype=torch.float64))
     with pytest.raises(ValueError, match="contiguous"):
         px.perm_sample_histogram(torch.zeros(8, dtype=torch.complex128)[::2], [0.0, 1.0])
+
+
+def test_binding_rejects_tensors_on_another_device(px, monkeypatch):
+    """Every tensor of a call, and a torch stream given to it, must be on the
+    current device (where the library launches): a tensor on another GPU is
+    refused before its pointer reaches the C-ABI.  CPU-only: tensors that
+    report a CUDA device stand in for real ones."""
+    import torch
+
+    class FakeCuda(torch.Tensor):
+        @property
+        def is_cuda(self):
+            return True
+
+        @property
+        def device(self):
+            return torch.device("cuda", self._dev)
+
+    def on(t, dev):
+        f = t.as_subclass(FakeCuda)
+        f._dev = dev
+        return f
+
+    class FakeStream:
+        def __init__(self, dev):
+            self.device = torch.device("cuda", dev)
+            self.cuda_stream = 0
+
+    monkeypatch.setattr(px, "_current_device", lambda: 0)
+    n, off = [3], [0]
+    c = torch.zeros(9, dtype=torch.complex128)
+    o = torch.zeros(1, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="A is on cuda:1"):
+        px.perm_c128(on(c, 1), n, off, on(o, 0))
+    with pytest.raises(ValueError, match="out is on cuda:1"):
+        px.perm_c128(on(c, 0), n, off, on(o, 1))
+    with pytest.raises(ValueError, match="current device is cuda:0"):
+        px.perm_f64(on(torch.zeros(9, dtype=torch.float64), 2), n, off, on(torch.zeros(1, dtype=torch.float64), 2))
+    with pytest.raises(ValueError, match="cuda:1"):
+        px.perm_modp(on(torch.zeros(9, dtype=torch.int32), 0), n, off, [7], on(torch.zeros(1, dtype=torch.int32), 1))
+    with pytest.raises(ValueError, match="stream is on cuda:1"):
+        px._stream(FakeStream(1))
+    assert px._stream(FakeStream(0)) == 0
+    with pytest.raises(ValueError, match="U is on cuda:3"):
+        px.perm_gather(on(torch.zeros((4, 4), dtype=torch.complex128), 3), [[0, 1]], [[1, 2]],
+                       on(torch.zeros(1, dtype=torch.complex128), 0))
+    with pytest.raises(ValueError, match="values is on cuda:1"):
+        px.perm_sample_stats(on(torch.zeros(4, dtype=torch.complex128), 1))

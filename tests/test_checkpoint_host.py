@@ -46,3 +46,33 @@ def test_unreadable_checkpoint_path_is_an_error(px, tmp_path):
         px.perm_schur_crt_ex(19, 0, str(f / "run.ckpt"))
     assert e.value.code == px.PERMX_EIO
     assert "cannot read checkpoint" in px.last_error()
+
+
+def _ckpt(body: str) -> str:
+    h = 1469598103934665603
+    for c in body.encode():
+        h ^= c
+        h = (h * 1099511628211) % (1 << 64)
+    return body + "sum %016x\n" % h
+
+
+def test_checkpoint_with_impossible_state_rejected(px, tmp_path):
+    """A checkpoint with a valid checksum and matching run, but a cursor at or
+    past the end of the walk (2^(n-1) Gray indices), a partial sum or a
+    finished residue not below its prime, is an I/O error before any GPU work;
+    such a cursor would otherwise never advance."""
+    n = 19
+    k = px.perm_schur_prime_count(n)
+    primes = px.perm_primes_1_mod_n(n, k + 1)
+    head = "permx-schur-ckpt 2\nn %d\nprimes %d %s\n" % (n, len(primes), " ".join(map(str, primes)))
+    cases = {
+        "cursor": head + "done 0\ncursor %d 0\n" % (1 << (n - 1)),
+        "partial": head + "done 0\ncursor 4096 %d\n" % primes[0],
+        "residue": head + "done 1 %d\ncursor 0 0\n" % primes[0],
+    }
+    for what, body in cases.items():
+        ck = tmp_path / f"{what}.ckpt"
+        ck.write_text(_ckpt(body))
+        with pytest.raises(px.PermxError) as e:
+            px.perm_schur_crt_ex(n, 0, str(ck))
+        assert e.value.code == px.PERMX_EIO, what

@@ -1,7 +1,6 @@
 """Continuous-batching server (serve_*): results equal the batched path bit for
 bit whether a request runs alone or in a mix, requests admitted while others
 run overlap with them, and admission limits behave."""
-import ctypes
 import time
 
 import numpy as np
@@ -14,52 +13,28 @@ pytestmark = pytest.mark.gpu
 
 
 class Server:
+    """Test adapter over the binding's Server: calls return the C-ABI codes
+    instead of raising, so the tests can check error paths."""
+
     def __init__(self, px, **cfg):
         self.px = px
-        self.lib = px._lib
-        self.lib.serve_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
-        self.lib.serve_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_void_p,
-                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
-        self.lib.serve_poll_timed.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
-                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
-                                              ctypes.POINTER(ctypes.c_int64)]
-        self.lib.serve_drain.argtypes = [ctypes.c_void_p, ctypes.c_int64]
-        self.lib.serve_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
-        self.lib.serve_destroy.argtypes = [ctypes.c_void_p]
-        buf = bytearray(40)
-        vals = [cfg.get("max_requests", 0), cfg.get("max_resident", 0)]
-        import struct
-        struct.pack_into("<iiqqii", buf, 0, vals[0], vals[1], cfg.get("device_bytes", 0),
-                         cfg.get("chunks_per_step", 0), 0, cfg.get("plain_fifo", 0))
-        self._cfg = (ctypes.c_char * 40).from_buffer(buf)
-        self.h = ctypes.c_void_p()
-        assert self.lib.serve_create(ctypes.addressof(self._cfg), ctypes.byref(self.h)) == 0, px.last_error()
+        self.S = px.Server(**cfg)
+        self.lib, self.h = px._lib, self.S.h
 
     def submit(self, A, field, p=0):
-        if field == 2:
-            buf = np.ascontiguousarray(A, np.uint32)
-        elif field == 0:
-            buf = np.ascontiguousarray(A, np.complex128)
-        else:
-            buf = np.ascontiguousarray(A, np.float64)
-        t = ctypes.c_uint64()
-        rc = self.lib.serve_submit(self.h, field, A.shape[0], buf.ctypes.data, p, ctypes.byref(t))
-        return rc, t.value
+        try:
+            return 0, self.S.submit(A, field, p)
+        except self.px.PermxError as e:
+            return e.code, 0
 
     def poll(self, ticket, field):
-        res = (ctypes.c_char * 16)()
-        done, ts, td = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int64(0)
-        rc = self.lib.serve_poll_timed(self.h, ticket, res, ctypes.byref(done), ctypes.byref(ts), ctypes.byref(td))
-        if rc or not done.value:
-            return rc, None, None
-        raw = bytes(res)
-        if field == 0:
-            v = complex(*np.frombuffer(raw, np.float64, 2))
-        elif field == 1:
-            v = float(np.frombuffer(raw[:8], np.float64)[0])
-        else:
-            v = int(np.frombuffer(raw[:4], np.uint32)[0])
-        return 0, v, (td.value - ts.value) * 1e-9
+        try:
+            r = self.S.poll(ticket)
+        except self.px.PermxError as e:
+            return e.code, None, None
+        if r is None:
+            return 0, None, None
+        return 0, r[0], r[1]
 
     def wait(self, tickets, timeout=120.0):
         out = {}
@@ -77,12 +52,11 @@ class Server:
         return out
 
     def stats(self):
-        s = (ctypes.c_int64 * 5)()
-        assert self.lib.serve_stats(self.h, s) == 0
-        return list(s)
+        st = self.S.stats()
+        return [st[k] for k in ("submitted", "completed", "resident", "steps", "launches")]
 
     def close(self):
-        self.lib.serve_destroy(self.h)
+        self.S.close()
 
 
 def _batched(px, A, field, p=0):
@@ -298,3 +272,60 @@ def test_max_size_requests_served_with_small_ones(px):
             assert res[t][0] == _batched(px, A, 1)
     finally:
         S.close()
+
+
+def test_work_budget_admission_lets_small_requests_pass(px):
+    """Admission by outstanding work: with a budget that holds one large
+    request, the second large one waits until the first one's steps have run,
+    while small requests queued behind it are admitted and finish first;
+    every result equals the batched path's."""
+    big = [ensemble("haar_u", 26, 1, seed=600 + i)[0] for i in range(2)]
+    cost_big = 26 * 2 ** 25                           # complex128-term equivalents of one n = 26 walk
+    S = Server(px, work_budget=cost_big + cost_big // 2)
+    try:
+        tb = []
+        for A in big:
+            rc, t = S.submit(A, 0)
+            assert rc == 0, px.last_error()
+            tb.append((t, 0))
+        small = [ensemble("goe", 12, 1, seed=700 + i)[0] for i in range(16)]
+        ts = []
+        for A in small:
+            rc, t = S.submit(A, 1)
+            assert rc == 0
+            ts.append((t, 1))
+        res = S.wait(tb + ts)
+        # the second large request starts only after the first one's work has run
+        assert res[tb[1][0]][1] > res[tb[0][0]][1]
+        assert max(res[t][1] for t, _ in ts) < res[tb[1][0]][1]
+        for A, (t, _) in zip(big, tb):
+            assert res[t][0] == _batched(px, A, 0)
+        for A, (t, _) in zip(small, ts):
+            assert res[t][0] == _batched(px, A, 1)
+        st = S.S.stats()
+        assert st["completed"] == 18 and st["pending"] == 0 and st["resident"] == 0
+        assert st["resident_work"] == 0
+        assert 0.0 < st["gpu_busy_ms"] <= st["uptime_ms"]
+    finally:
+        S.close()
+
+
+def test_unlimited_and_tiny_budgets_give_the_same_bits(px):
+    """The work budget changes only when requests run, never their results:
+    an unlimited budget and one smaller than any request (one request
+    resident at a time) serve a mixed trace bit-identically."""
+    reqs = _mix(11, 24)
+    out = []
+    for budget in (-1, 1):
+        S = Server(px, work_budget=budget)
+        try:
+            tickets = []
+            for A, f, p in reqs:
+                rc, t = S.submit(A, f, p)
+                assert rc == 0, px.last_error()
+                tickets.append((t, f))
+            res = S.wait(tickets)
+            out.append([res[t][0] for t, _ in tickets])
+        finally:
+            S.close()
+    assert out[0] == out[1]
