@@ -650,7 +650,7 @@ def _drive(S, reqs, arrivals):
     return lat, time.perf_counter() - t0, results
 
 
-def served_object(scale: float = 1.0) -> dict:
+def served_object(scale: float = 1.0, work_budget: int = 0) -> dict:
     """Config 4: a Poisson stream of 20,000 requests (x scale) at 70 % of the
     measured capacity, mixing complex128 Haar n ~ U[10,26], float64 GOE
     n ~ U[10,26], complex128 cycle-geodesic points (odd n in [9,25], t on the
@@ -670,7 +670,7 @@ def served_object(scale: float = 1.0) -> dict:
         cal = reqs[: max(100, count // 5)]
         sat = {}
         for name, plain in (("continuous", False), ("plain_fifo", True)):
-            S = px.Server(device_bytes=4 << 30, plain_fifo=plain)
+            S = px.Server(device_bytes=4 << 30, plain_fifo=plain, work_budget=work_budget)
             _, span, _ = _drive(S, cal, [0.0] * len(cal))
             st = S.stats()
             S.close()
@@ -680,7 +680,7 @@ def served_object(scale: float = 1.0) -> dict:
         arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
         out, vals = {}, {}
         for name, plain in (("continuous", False), ("plain_fifo", True)):
-            S = px.Server(device_bytes=4 << 30, plain_fifo=plain)
+            S = px.Server(device_bytes=4 << 30, plain_fifo=plain, work_budget=work_budget)
             lat, span, res = _drive(S, reqs, arrivals)
             st = S.stats()
             S.close()
@@ -712,7 +712,7 @@ def served_object(scale: float = 1.0) -> dict:
                        "mix": "1/4 each: c128 Haar n~U[10,26], f64 GOE n~U[10,26], c128 cycle geodesic odd n in "
                               "[9,25] t in k/200, F_p random n~U[16,30] with the largest p = 1 (mod n) < 2^31",
                        "load": "0.7 x the continuous server's saturated rate", "scale_of_20000": scale,
-                       "work_budget": "automatic (2^33 complex128-term equivalents)"}}
+                       "work_budget": work_budget or "automatic (2^35 complex128-term equivalents)"}}
 
 
 def serving(args):

@@ -339,7 +339,7 @@ typedef struct {
     int32_t device;              /* CUDA device ordinal */
     int32_t plain_fifo;          /* 1 = baseline: one request at a time, one launch per request */
     int64_t work_budget;         /* outstanding work admitted at once, in complex128-term equivalents
-                                    (0 = automatic, 2^33, about 30 ms of the GPU; < 0 = no limit) */
+                                    (0 = automatic, 2^35, about 130 ms of the GPU; < 0 = no limit) */
 } perm_serve_cfg;
 
 /* Counters of a server (serve_stats2). */

@@ -104,7 +104,7 @@ struct StepBuf {
 using namespace permx;
 
 constexpr int kSideStreams = 4;
-constexpr int64_t kDefaultWorkBudget = (int64_t)1 << 33;
+constexpr int64_t kDefaultWorkBudget = (int64_t)1 << 35;
 constexpr int64_t kBypassNs = 20'000'000;   // how long a request that does not fit lets others pass
 constexpr size_t kAdmitLookahead = 1024;     // queued requests examined per admission
 
