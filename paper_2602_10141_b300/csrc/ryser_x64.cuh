@@ -5,17 +5,22 @@
 // multiplies and adds issue at 1/2 to 1/1 of it.  This walk therefore keeps
 // everything in integers:
 //  - row i is scaled by 2^sigma_i (sum_j |a_ij| 2^sigma_i < 2^61) and rounded
-//    to even int64 entries A_ij, so every Gray-walk row sum
-//    R_i = X_i + sum_{j in S} A_ij is exact (no drift, no rounding);
+//    to even int64 entries A_ij (each entry moves by at most
+//    2^-60 sum_j |a_ij|), so every Gray-walk row sum
+//    R_i = X_i + sum_{j in S} A_ij of the rounded matrix is exact (no drift);
 //  - a product of row sums is a float with a signed 62-bit mantissa m
 //    (|m| in [2^61, 2^62], complex: the larger component in [2^60, 2^61]) and
 //    an int exponent; each factor is one truncated 64x64 -> 128-bit product
 //    from three signed 32x32 -> 64-bit multiplies, then a leading-zero
-//    normalisation;
-//  - each chunk sums its terms exactly into a 128-bit fixed-point
-//    accumulator whose exponent follows the chunk's first term, and hands the
-//    chunk total on as a double-double scaled back by 2^-sum(sigma).
-// Relative precision per factor is about 2^-59 (float64: 2^-53).
+//    normalisation, so a term carries a truncation error of at most
+//    4n 2^-59 (real) or 16n 2^-59 (complex) times sum_i prod_{k != i} |R_k|;
+//  - each chunk adds its terms into a 128-bit fixed-point accumulator whose
+//    grid follows the chunk's first term (error at most 2^-80 of the sum of
+//    the term magnitudes), and hands the chunk total on as a double-double
+//    scaled back by 2^-sum(sigma).
+// The result is therefore not exact; relative precision per factor is about
+// 2^-58 (float64: 2^-53), and the tests check these bounds against exact
+// rational arithmetic.
 #pragma once
 #include "common.cuh"
 #include "ryser_fp.cuh"
@@ -23,7 +28,7 @@
 
 namespace permx {
 
-// Exact reduction of the lanes' chunk accumulators over aligned groups of
+// Reduction of the lanes' chunk accumulators over aligned groups of
 // `lanes` lanes (xor butterfly of symmetric merges), in integers: the
 // double-double conversion then happens once per group instead of once per
 // chunk, which keeps the slow FP64 pipe out of the per-chunk path.

@@ -125,7 +125,7 @@ __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t 
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
 }
 
-// Exact fixed-point sum of one chunk's terms: value = acc * 2^E.  The first
+// Fixed-point sum of one chunk's terms: value = acc * 2^E.  The first
 // term fixes E 24 bits below its mantissa's lowest bit range; a term more
 // than 2^40 above the accumulator scale rescales it first, so at most 2^12
 // terms never overflow 128 bits.  Terms far below (shift < -62) round to 0.
