@@ -48,13 +48,16 @@ def _load() -> ctypes.CDLL:
     sig = {
         "perm_last_error": ([], ctypes.c_char_p),
         "permx_version": ([], ctypes.c_char_p),
-        "perm_c128": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
-        "perm_f64": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
-        "perm_modp": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
+        # host arrays of the batched calls travel as raw addresses (numpy .ctypes.data):
+        # these run once per matrix in one-call-per-matrix use, where ctypes pointer
+        # objects cost more than the launch
+        "perm_c128": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
+        "perm_f64": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
+        "perm_modp": ([vp, vp, vp, vp, i64, vp, vp], ctypes.c_int),
         "perm_c128_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
         "perm_f64_host": ([vp, P(i32), P(i64), i64, vp, vp], ctypes.c_int),
         "perm_modp_host": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
-        "perm_modp_noalloc": ([vp, P(i32), P(i64), P(u32), i64, vp, vp], ctypes.c_int),
+        "perm_modp_noalloc": ([vp, vp, vp, vp, i64, vp, vp], ctypes.c_int),
         "perm_modp_gray_range": ([vp, i32, u32, u64, u64, P(u32), vp], ctypes.c_int),
         "perm_schur_crt": ([i32, i32, ctypes.c_char_p, P(i64), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "perm_schur_crt_ex": ([i32, i32, ctypes.c_char_p, u64, i64, P(i64), ctypes.c_char_p, ctypes.c_size_t,
@@ -168,19 +171,27 @@ def _need(n: np.ndarray, offset: np.ndarray, max_n: int) -> int:
     the library accepts (it rejects the others itself, with PERMX_EINVAL)."""
     if len(n) != len(offset):
         raise ValueError(f"n has {len(n)} entries, offset {len(offset)}")
+    if len(n) <= 8:                  # a handful of matrices: plain Python beats numpy's per-call cost
+        need = 0
+        for k, o in zip(n.tolist(), offset.tolist()):
+            if 1 <= k <= max_n:
+                need = max(need, o + k * k)
+        return need
     ok = (n >= 1) & (n <= max_n)
     if not ok.any():
         return 0
     return int(np.max(offset[ok].astype(np.int64) + n[ok].astype(np.int64) ** 2))
 
 
+_DTYPES: dict = {}
+
+
 def _dtypes(kind: str):
-    import torch
-    if kind == "c128":
-        return (torch.complex128,)
-    if kind == "f64":
-        return (torch.float64,)
-    return tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
+    if not _DTYPES:
+        import torch
+        _DTYPES.update({"c128": (torch.complex128,), "f64": (torch.float64,),
+                        "modp": tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)})
+    return _DTYPES[kind]
 
 
 def _tensors(*specs) -> None:
@@ -209,7 +220,7 @@ def _on_current_device(*named) -> None:
             raise ValueError(f"{what} must be on a CUDA device")
     cur = _current_device()
     for t, what in named:
-        idx = t.device.index
+        idx = t.get_device()
         if idx != cur:
             raise ValueError(f"{what} is on cuda:{idx}, the current device is cuda:{cur}; "
                              "all tensors of a call must be on the current device")
@@ -223,8 +234,7 @@ def perm_c128(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
     """out[b] = perm of the n[b] x n[b] complex128 matrix at A.view(-1)[offset[b]:]."""
     n, offset = _i32(n), _i64(offset)
     _tensors((A, "A", "c128", _need(n, offset, MAX_N_FP)), (out, "out", "c128", len(n)))
-    _check(_lib.perm_c128(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
-                          out.data_ptr(), _stream(stream)))
+    _check(_lib.perm_c128(A.data_ptr(), n.ctypes.data, offset.ctypes.data, len(n), out.data_ptr(), _stream(stream)))
     return out
 
 
@@ -232,8 +242,7 @@ def perm_f64(A, n: Sequence[int], offset: Sequence[int], out, stream=None):
     """out[b] = perm of the n[b] x n[b] float64 matrix at A.view(-1)[offset[b]:]."""
     n, offset = _i32(n), _i64(offset)
     _tensors((A, "A", "f64", _need(n, offset, MAX_N_FP)), (out, "out", "f64", len(n)))
-    _check(_lib.perm_f64(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64), len(n),
-                         out.data_ptr(), _stream(stream)))
+    _check(_lib.perm_f64(A.data_ptr(), n.ctypes.data, offset.ctypes.data, len(n), out.data_ptr(), _stream(stream)))
     return out
 
 
@@ -241,8 +250,8 @@ def perm_modp(A, n: Sequence[int], offset: Sequence[int], p: Sequence[int], out,
     """A: device int32/uint32 residues (< p[b]); out: device int32 tensor of residues."""
     n, offset, p = _i32(n), _i64(offset), _u32(p)
     _tensors((A, "A", "modp", _need(n, offset, MAX_N_MODP)), (out, "out", "modp", len(n)))
-    _check(_lib.perm_modp(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
-                          _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
+    _check(_lib.perm_modp(A.data_ptr(), n.ctypes.data, offset.ctypes.data, p.ctypes.data, len(n), out.data_ptr(),
+                          _stream(stream)))
     return out
 
 
@@ -533,8 +542,8 @@ def perm_modp_noalloc(A, n: Sequence[int], offset: Sequence[int], p: Sequence[in
     intermediates in the library's fixed device array (see include/permx.h)."""
     n, offset, p = _i32(n), _i64(offset), _u32(p)
     _tensors((A, "A", "modp", _need(n, offset, MAX_N_MODP)), (out, "out", "modp", len(n)))
-    _check(_lib.perm_modp_noalloc(A.data_ptr(), _p(n, ctypes.c_int32), _p(offset, ctypes.c_int64),
-                                  _p(p, ctypes.c_uint32), len(n), out.data_ptr(), _stream(stream)))
+    _check(_lib.perm_modp_noalloc(A.data_ptr(), n.ctypes.data, offset.ctypes.data, p.ctypes.data, len(n),
+                                  out.data_ptr(), _stream(stream)))
     return out
 
 

@@ -53,15 +53,24 @@ def _gen_dispatch() -> None:
         out += [f"cudaError_t dispatch_{kind}(int n, const {lt}& L, cudaStream_t s) {{",
                 "    const uint64_t items = L.item_end - L.item_begin;",
                 "    if (items == 0) return cudaSuccess;",
+                "    // blocks of kRyserThreads threads while the launch fills every SM; a",
+                "    // smaller launch takes smaller blocks (down to one warp) so that its",
+                "    // warps spread over more SMs instead of sharing a few (the results do",
+                "    // not depend on the block size)",
+                "    int threads = kRyserThreads;",
                 "    auto grid_for = [&](int bps, int lanes_per_item = 1) {",
-                "        uint64_t want = (items * lanes_per_item + kRyserThreads - 1) / kRyserThreads;",
-                "        uint64_t cap = (uint64_t)sm_count() * (uint64_t)bps;",
+                "        const uint64_t lanes = items * lanes_per_item;",
+                "        const uint64_t sms = (uint64_t)sm_count();",
+                "        while (threads > 32 && (lanes + threads - 1) / threads < sms) threads >>= 1;",
+                "        uint64_t want = (lanes + threads - 1) / threads;",
+                "        uint64_t cap = sms * (uint64_t)bps * (uint64_t)(kRyserThreads / threads);",
                 "        return (int)(want < cap ? want : cap);",
                 "    };",
                 "    switch (n) {"]
         for n in range(1, mx + 1):
             lanes = f"x64c_paired({n}) ? 2 : 1" if kind == "x64c" else "1"
-            out.append(f"        case {n}: return launch_{kind}<{n}>(L, grid_for(blocks_per_sm_{kind}<{n}>(), {lanes}), s);")
+            out.append(f"        case {n}: {{ const int g = grid_for(blocks_per_sm_{kind}<{n}>(), {lanes}); "
+                       f"return launch_{kind}<{n}>(L, g, threads, s); }}")
         out += ["        default: return cudaErrorInvalidValue;", "    }", "}", ""]
     # resident blocks per SM of the kernel that a (kind, n) launch uses
     out += ["int dispatch_blocks_per_sm(int kind, int n) {",

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <atomic>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -17,6 +18,8 @@
 
 #include "batch.h"
 #include "common.cuh"
+#include "finalize.cuh"
+#include "x64_arith.cuh"
 
 namespace permx {
 
@@ -120,25 +123,24 @@ int sm_count() {
 // device kernels: staging and finalisation
 // ---------------------------------------------------------------------------
 
-// Integer-mantissa staging (one block per matrix): row i gets the scale
+// Integer-mantissa staging of one matrix by one block: row i gets the scale
 // sigma_i = 60 - floor(log2(sum_j |a_ij|)) (complex: |re| + |im|), entries
 // A_ij = 2 round(a_ij 2^(sigma_i - 1)) (even, so halves are exact), the
 // Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij)/2, zero padding, and
 // one trailing word with -sum_i sigma_i.  W = int64 words per entry.  The
 // matrix is read once into shared memory; the row scales take one thread per
-// row (the float sum in column order), the conversions one thread per entry.
+// row (the float sum in column order), the conversions one thread per entry,
+// in integer operations.
 constexpr int kStageX64Threads = 128;
 template <int W>
-__global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const double* __restrict__ A,
-                                                                   const StageDesc* __restrict__ d,
-                                                                   int64_t* __restrict__ colT) {
+__device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, const StageDesc s,
+                                                int64_t* __restrict__ colT) {
     // the matrix, row-major: the float entries, each replaced in place by its
     // integer A_ij once the row scales are known
     __shared__ long long buf[PERMX_MAX_N_FP * PERMX_MAX_N_FP * W];
     __shared__ int sig_row[PERMX_MAX_N_FP];   // sigma_i, or kNonFinite
     __shared__ int sig_sum, bad;
     constexpr int kNonFinite = -1 << 30;
-    const StageDesc s = d[blockIdx.x];
     const int n = s.n, ld = s.ld, nw = n * W, tot = n * nw;
     int64_t* base = colT + s.dst * W;   // dst counts entries of W words
     const long long* src = reinterpret_cast<const long long*>(A + s.src * W);
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const doubl
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
         const int i = e / nw, jw = e - i * nw, j = jw / W, w = jw - j * W;
         const int sig = sig_row[i];
-        const int64_t a = sig != kNonFinite ? 2 * (int64_t)llrint(ldexp(__longlong_as_double(buf[e]), sig - 1)) : 0;
+        const int64_t a = sig != kNonFinite ? 2 * x64_scaled_round(__longlong_as_double(buf[e]), sig - 1) : 0;
         buf[e] = a;
         base[((int64_t)j * ld + i) * W + w] = a;
     }
@@ -186,6 +188,13 @@ __global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const doubl
         base[(int64_t)(n + 1) * ld * W] = -(int64_t)sig_sum;
         base[(int64_t)(n + 1) * ld * W + 1] = bad;   // 1: non-finite entry, result NaN
     }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const double* __restrict__ A,
+                                                                   const StageDesc* __restrict__ d,
+                                                                   int64_t* __restrict__ colT) {
+    stage_x64_block<W>(A, d[blockIdx.x], colT);
 }
 
 // x_i = a_{i,n-1} - (1/2) sum_j a_ij for the Nijenhuis-Wilf form.
@@ -225,8 +234,7 @@ __device__ __forceinline__ double staged_entry(double v, uint32_t) { return v; }
 __device__ __forceinline__ double2 staged_entry(double2 v, uint32_t) { return v; }
 
 template <typename T>
-__global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
-    const StageDesc s = d[blockIdx.x];
+__device__ __forceinline__ void stage_columns_block(const T* __restrict__ A, const StageDesc s, T* __restrict__ colT) {
     const int n = s.n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
@@ -241,8 +249,43 @@ __global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* _
             colT[s.dst + (int64_t)n * s.ld + i] = i < n ? x_entry(A + s.src + (int64_t)i * n, n, s.p) : T{};
 }
 
-__device__ __forceinline__ uint32_t mulmod_u64(uint64_t a, uint64_t b, uint32_t p) {
-    return (uint32_t)((a % p) * (b % p) % p);
+template <typename T>
+__global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
+    stage_columns_block<T>(A, d[blockIdx.x], colT);
+}
+
+// Set-up of a call whose metadata is small enough to travel as a kernel
+// parameter: block 0 writes the metadata into the workspace and clears the
+// words that must start at zero (F_p accumulators, the groups' finalisation
+// tickets); block b stages matrix b from its descriptor in the parameter.
+// One launch where an upload and a staging launch would otherwise run.
+template <int SZ>
+struct alignas(16) MetaBytes {
+    uint32_t words, pad_[3];
+    uint32_t w[SZ / 4];        // 16-byte aligned: the descriptors read from it hold 8-byte fields
+};
+static_assert(offsetof(MetaBytes<1024>, w) % 16 == 0, "metadata words must be 16-byte aligned");
+template <int SZ>
+__device__ __forceinline__ void setup_meta(const MetaBytes<SZ>& m, uint32_t* __restrict__ dst, uint32_t zero_from,
+                                           uint32_t zero_words) {
+    if (blockIdx.x != 0) return;
+    for (uint32_t i = threadIdx.x; i < m.words; i += blockDim.x) dst[i] = m.w[i];
+    for (uint32_t i = threadIdx.x; i < zero_words; i += blockDim.x) dst[zero_from + i] = 0;
+}
+template <int SZ, typename T>
+__global__ void setup_columns_kernel(const T* __restrict__ A, const __grid_constant__ MetaBytes<SZ> m,
+                                     uint32_t* __restrict__ ws, uint32_t zero_from, uint32_t zero_words,
+                                     T* __restrict__ colT) {
+    setup_meta(m, ws, zero_from, zero_words);
+    stage_columns_block<T>(A, reinterpret_cast<const StageDesc*>(m.w)[blockIdx.x], colT);
+}
+template <int SZ, int W>
+__global__ void __launch_bounds__(kStageX64Threads) setup_x64_kernel(const double* __restrict__ A,
+                                                                   const __grid_constant__ MetaBytes<SZ> m,
+                                                                   uint32_t* __restrict__ ws, uint32_t zero_from,
+                                                                   uint32_t zero_words, int64_t* __restrict__ colT) {
+    setup_meta(m, ws, zero_from, zero_words);
+    stage_x64_block<W>(A, reinterpret_cast<const StageDesc*>(m.w)[blockIdx.x], colT);
 }
 
 __global__ void finalize_modp_kernel(const unsigned long long* __restrict__ acc, const ModpFinal* __restrict__ f,
@@ -250,78 +293,16 @@ __global__ void finalize_modp_kernel(const unsigned long long* __restrict__ acc,
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= count) return;
     const ModpFinal x = f[b];
-    uint32_t v = mulmod_u64(acc[b] % x.p, x.rfix, x.p);
-    if (x.negate && v) v = x.p - v;
-    out[x.out_index] = v;
+    out[x.out_index] = finalize_modp_value(acc[b], x);
 }
 
-__device__ __forceinline__ void dd_pair_add(double& s, double& c, double s2, double c2) {
-    double t = s + s2;
-    double bp = t - s;
-    double err = (s - (t - bp)) + (s2 - bp);
-    s = t;
-    c = (c + c2) + err;
-}
-
-// One block (kFinalThreads threads) per matrix; thread t folds partials
-// t, t + kFinalThreads, ... in order, then a fixed binary tree (level h adds
-// thread t + h into thread t).  Threads at or past the partial count hold the
-// pair (0, 0), and adding it leaves a pair unchanged, so the tree starts at
-// the first level whose upper half holds partials; its last five levels run
-// in warp 0 with shuffles.  FP64 is slow on B300, so the levels a lone small
-// matrix skips are most of this kernel's time.
-constexpr int kFinalThreads = 128;
+// One block (kFinalThreads threads) per matrix: the fixed-order double-double
+// sum of its partial slots (finalize_fp_block).
 __global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double* __restrict__ partial,
                                                                     const FpFinal* __restrict__ f,
                                                                     int cplx, void* __restrict__ out) {
     __shared__ double sh[4][kFinalThreads];
-    const FpFinal x = f[blockIdx.x];
-    const int w = cplx ? 4 : 2;
-    double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
-    for (int64_t q = threadIdx.x; q < x.count; q += kFinalThreads) {
-        const double* pq = partial + (x.first + q) * w;
-        dd_pair_add(s0, c0, pq[0], pq[1]);
-        if (cplx) dd_pair_add(s1, c1, pq[2], pq[3]);
-    }
-    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = c0; sh[2][threadIdx.x] = s1; sh[3][threadIdx.x] = c1;
-    __syncthreads();
-    const int live = x.count < kFinalThreads ? (int)x.count : kFinalThreads;
-    int h = kFinalThreads / 2;
-    while (h > 0 && h >= live) h >>= 1;       // levels that would add only (0, 0) pairs
-    for (; h >= 32; h >>= 1) {
-        if (threadIdx.x < h) {
-            double a = sh[0][threadIdx.x], ac = sh[1][threadIdx.x];
-            dd_pair_add(a, ac, sh[0][threadIdx.x + h], sh[1][threadIdx.x + h]);
-            sh[0][threadIdx.x] = a; sh[1][threadIdx.x] = ac;
-            if (cplx) {
-                double b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
-                dd_pair_add(b, bc, sh[2][threadIdx.x + h], sh[3][threadIdx.x + h]);
-                sh[2][threadIdx.x] = b; sh[3][threadIdx.x] = bc;
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < 32) {
-        double a = sh[0][threadIdx.x], ac = sh[1][threadIdx.x], b = sh[2][threadIdx.x], bc = sh[3][threadIdx.x];
-        for (; h > 0; h >>= 1) {
-            const double a2 = __shfl_down_sync(0xffffffffu, a, h), ac2 = __shfl_down_sync(0xffffffffu, ac, h);
-            const double b2 = __shfl_down_sync(0xffffffffu, b, h), bc2 = __shfl_down_sync(0xffffffffu, bc, h);
-            if (threadIdx.x < h) {
-                dd_pair_add(a, ac, a2, ac2);
-                if (cplx) dd_pair_add(b, bc, b2, bc2);
-            }
-        }
-        if (threadIdx.x == 0) {
-            const double sg = (x.negate ? -1.0 : 1.0) * (x.twice ? 2.0 : 1.0);
-            const double re = sg * (a + ac);
-            if (cplx) {
-                const double im = sg * (b + bc);
-                reinterpret_cast<double2*>(out)[x.out_index] = make_double2(re, im);
-            } else {
-                reinterpret_cast<double*>(out)[x.out_index] = re;
-            }
-        }
-    }
+    finalize_fp_block(partial, f[blockIdx.x], cplx, out, sh);
 }
 
 // Server variant: accumulators and outputs at arbitrary indices.
@@ -330,9 +311,8 @@ __global__ void finalize_modp_at_kernel(const unsigned long long* __restrict__ a
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= count) return;
     const ModpFinalAt x = f[b];
-    uint32_t v = mulmod_u64(acc[x.acc_index] % x.p, x.rfix, x.p);
-    if (x.negate && v) v = x.p - v;
-    out[x.out_index] = v;
+    const ModpFinal y{x.p, x.rfix, x.negate, 0, x.out_index};
+    out[x.out_index] = finalize_modp_value(acc[x.acc_index], y);
 }
 
 cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t count, void* colT, cudaStream_t s) {
@@ -504,41 +484,16 @@ static int alloc_ws(Workspace& ws, size_t bytes, cudaStream_t s) {
     return PERMX_OK;
 }
 
-// Metadata of small batches travels as a kernel parameter (by value) and is
-// written into the workspace on the device: the call then stays fully
-// asynchronous, where a copy from pageable host memory would synchronise the
-// stream first.
-template <int SZ>
-struct MetaBytes {
-    uint32_t words;
-    uint32_t w[SZ / 4];
-};
-template <int SZ>
-__global__ void meta_copy_kernel(const MetaBytes<SZ> m, uint32_t* __restrict__ dst) {
-    for (uint32_t i = threadIdx.x; i < m.words; i += blockDim.x) dst[i] = m.w[i];
-}
-template <int SZ>
-static cudaError_t meta_copy(const std::vector<unsigned char>& host, void* dst, cudaStream_t s) {
-    MetaBytes<SZ> m;
-    m.words = (uint32_t)((host.size() + 3) / 4);
-    std::memset(m.w, 0, sizeof m.w);
-    std::memcpy(m.w, host.data(), host.size());
-    meta_copy_kernel<SZ><<<1, 256, 0, s>>>(m, static_cast<uint32_t*>(dst));
-    return cudaGetLastError();
-}
-static cudaError_t upload_meta(const std::vector<unsigned char>& host, void* dst, cudaStream_t s) {
-    if (host.size() <= 1024) return meta_copy<1024>(host, dst, s);
-    if (host.size() <= 4096) return meta_copy<4096>(host, dst, s);
-    if (host.size() <= 16384) return meta_copy<16384>(host, dst, s);
-    return cudaMemcpyAsync(dst, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-}
-
 // ---------------------------------------------------------------------------
 // prepare / execute / release.  prepare() plans the batch, allocates one
-// workspace and uploads the metadata; execute() only enqueues kernels and a
-// memset (so it can be captured in a CUDA graph and replayed); release()
-// returns the workspace.  The one-shot calls below run all three.
+// workspace and lays out the metadata (uploaded once, or kept on the host to
+// travel as a kernel parameter when it is at most kMetaByValue bytes);
+// execute() only enqueues kernels and memsets (so it can be captured in a
+// CUDA graph and replayed); release() returns the workspace.  The one-shot
+// calls below run all three.
 // ---------------------------------------------------------------------------
+constexpr size_t kMetaByValue = 16384;
+
 int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
                   cudaStream_t s, Prepared& X) {
     X = Prepared{};
@@ -546,6 +501,7 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
     X.batch = batch;
     X.P = plan_batch(n, batch, field);
     X.x64 = !X.P.groups.empty() && X.P.groups[0].x64;
+    const size_t ngroups = X.P.groups.size();
     std::vector<unsigned char> host;
     if (field == Field::MODP) {
         std::vector<StageDesc> stage(batch);
@@ -569,8 +525,10 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
         X.o_pinv = align256(X.o_p + 4 * batch);
         X.o_fin = align256(X.o_pinv + 4 * batch);
         X.o_meta_end = align256(X.o_fin + sizeof(ModpFinal) * batch);
-        X.o_acc = X.o_meta_end;
-        X.o_col = align256(X.o_acc + 8 * batch);
+        X.o_done = X.o_meta_end;
+        X.o_acc = align256(X.o_done + 4 * ngroups);
+        X.o_zero_end = X.o_acc + 8 * batch;
+        X.o_col = align256(X.o_zero_end);
         X.bytes = align256(X.o_col + 4 * (size_t)X.P.col_elems);
         host.resize(X.o_meta_end);
         std::memcpy(host.data() + X.o_stage, stage.data(), sizeof(StageDesc) * batch);
@@ -598,7 +556,9 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
         X.o_stage = 0;
         X.o_fin = align256(sizeof(StageDesc) * batch);
         X.o_meta_end = align256(X.o_fin + sizeof(FpFinal) * batch);
-        X.o_part = X.o_meta_end;
+        X.o_done = X.o_meta_end;
+        X.o_zero_end = X.o_done + 4 * ngroups;
+        X.o_part = align256(X.o_zero_end);
         X.o_col = align256(X.o_part + 8 * (size_t)pw * (size_t)X.P.total_partials);
         X.bytes = align256(X.o_col + 8 * (size_t)X.P.col_elems);
         host.resize(X.o_meta_end);
@@ -609,7 +569,11 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
     int rc = alloc_ws(ws, X.bytes, s);
     if (rc) return rc;
     X.ws = static_cast<unsigned char*>(ws.base);
-    cudaError_t e = upload_meta(host, X.ws, s);
+    if (host.size() <= kMetaByValue) {
+        X.meta = std::move(host);   // passed to the set-up kernel of every execution
+        return PERMX_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(X.ws, host.data(), host.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         release_batch(X, s);
         return cuda_fail(e, "metadata upload");
@@ -621,6 +585,68 @@ void release_batch(Prepared& X, cudaStream_t s) {
     if (X.ws) ws_free(X.ws, s);
     X.ws = nullptr;
 }
+
+namespace {
+
+template <int SZ>
+cudaError_t launch_setup_sz(const Prepared& X, const void* A, cudaStream_t s) {
+    MetaBytes<SZ> m;
+    std::memset(&m, 0, sizeof m);
+    m.words = (uint32_t)((X.meta.size() + 3) / 4);
+    std::memcpy(m.w, X.meta.data(), X.meta.size());
+    uint32_t* ws = reinterpret_cast<uint32_t*>(X.ws);
+    const uint32_t zf = (uint32_t)(X.o_done / 4), zw = (uint32_t)((X.o_zero_end - X.o_done + 3) / 4);
+    const unsigned grid = (unsigned)X.batch;
+    if (X.field == Field::MODP) {
+        setup_columns_kernel<SZ, uint32_t><<<grid, 256, 0, s>>>(static_cast<const uint32_t*>(A), m, ws, zf, zw,
+                                                                reinterpret_cast<uint32_t*>(X.ws + X.o_col));
+    } else if (X.x64) {
+        int64_t* col = reinterpret_cast<int64_t*>(X.ws + X.o_col);
+        if (X.field == Field::C128)
+            setup_x64_kernel<SZ, 2><<<grid, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), m, ws, zf, zw, col);
+        else
+            setup_x64_kernel<SZ, 1><<<grid, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), m, ws, zf, zw, col);
+    } else if (X.field == Field::C128) {
+        setup_columns_kernel<SZ, double2><<<grid, 256, 0, s>>>(static_cast<const double2*>(A), m, ws, zf, zw,
+                                                               reinterpret_cast<double2*>(X.ws + X.o_col));
+    } else {
+        setup_columns_kernel<SZ, double><<<grid, 256, 0, s>>>(static_cast<const double*>(A), m, ws, zf, zw,
+                                                              reinterpret_cast<double*>(X.ws + X.o_col));
+    }
+    return cudaGetLastError();
+}
+
+// Metadata, zeroed words and staging for one execution.
+cudaError_t launch_setup(const Prepared& X, const void* A, cudaStream_t s) {
+    if (!X.meta.empty()) {
+        if (X.meta.size() <= 1024) return launch_setup_sz<1024>(X, A, s);
+        if (X.meta.size() <= 4096) return launch_setup_sz<4096>(X, A, s);
+        return launch_setup_sz<16384>(X, A, s);
+    }
+    unsigned char* d = X.ws;
+    cudaError_t e = cudaMemsetAsync(d + X.o_done, 0, X.o_zero_end - X.o_done, s);
+    if (e != cudaSuccess) return e;
+    const StageDesc* sd = reinterpret_cast<const StageDesc*>(d + X.o_stage);
+    const unsigned grid = (unsigned)X.batch;
+    if (X.field == Field::MODP)
+        stage_columns_kernel<uint32_t><<<grid, 256, 0, s>>>(static_cast<const uint32_t*>(A), sd,
+                                                             reinterpret_cast<uint32_t*>(d + X.o_col));
+    else if (X.x64 && X.field == Field::C128)
+        stage_x64_kernel<2><<<grid, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), sd,
+                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+    else if (X.x64)
+        stage_x64_kernel<1><<<grid, kStageX64Threads, 0, s>>>(static_cast<const double*>(A), sd,
+                                                                reinterpret_cast<int64_t*>(d + X.o_col));
+    else if (X.field == Field::C128)
+        stage_columns_kernel<double2><<<grid, 256, 0, s>>>(static_cast<const double2*>(A), sd,
+                                                            reinterpret_cast<double2*>(d + X.o_col));
+    else
+        stage_columns_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double*>(A), sd,
+                                                           reinterpret_cast<double*>(d + X.o_col));
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t StreamSet::create(int dev) {
     device = dev;
@@ -713,23 +739,19 @@ cudaError_t launch_groups(const Prepared& X, cudaStream_t s, LaunchGroup&& launc
 
 int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
     unsigned char* d = X.ws;
-    const int64_t batch = X.batch;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = launch_setup(X, A, s);
+    const GroupPlan* g0 = X.P.groups.data();
+    unsigned* done = reinterpret_cast<unsigned*>(d + X.o_done);
     if (X.field == Field::MODP) {
-        e = cudaMemsetAsync(d + X.o_acc, 0, 8 * batch, s);
-        if (e == cudaSuccess) {
-            stage_columns_kernel<uint32_t><<<(unsigned)batch, 256, 0, s>>>(
-                static_cast<const uint32_t*>(A), reinterpret_cast<const StageDesc*>(d + X.o_stage),
-                reinterpret_cast<uint32_t*>(d + X.o_col));
-            e = cudaGetLastError();
-        }
+        const ModpFinal* fin = reinterpret_cast<const ModpFinal*>(d + X.o_fin);
+        unsigned long long* acc = reinterpret_cast<unsigned long long*>(d + X.o_acc);
         if (e == cudaSuccess)
             e = launch_groups(X, s, [&](const GroupPlan& g, cudaStream_t ls) {
                 ModpLaunch L;
                 L.colT = reinterpret_cast<const uint32_t*>(d + X.o_col) + g.col_off;
                 L.p = reinterpret_cast<const uint32_t*>(d + X.o_p) + g.first_mat;
                 L.pinv = reinterpret_cast<const uint32_t*>(d + X.o_pinv) + g.first_mat;
-                L.acc = reinterpret_cast<unsigned long long*>(d + X.o_acc) + g.first_mat;
+                L.acc = acc + g.first_mat;
                 L.mat_stride = g.mat_stride;
                 L.item_begin = 0;
                 L.item_end = (uint64_t)g.items;
@@ -738,36 +760,27 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
                 L.ell = g.ell;
                 L.log2_chunks = g.log2_chunks;
                 L.nw = g.nw;
-                return dispatch_modp(g.n, L, ls);
+                const int64_t count = (int64_t)g.mats.size();
+                if (count <= kFuseFinalMax) {     // the walk's last block finalises
+                    L.fin = fin + g.first_mat;
+                    L.nfin = (int)count;
+                    L.done = done + (&g - g0);
+                    L.out = static_cast<uint32_t*>(out);
+                    return dispatch_modp(g.n, L, ls);
+                }
+                cudaError_t f = dispatch_modp(g.n, L, ls);
+                if (f != cudaSuccess) return f;
+                finalize_modp_kernel<<<(unsigned)((count + 255) / 256), 256, 0, ls>>>(
+                    acc + g.first_mat, fin + g.first_mat, count, static_cast<uint32_t*>(out));
+                return cudaGetLastError();
             });
-        if (e == cudaSuccess) {
-            finalize_modp_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(
-                reinterpret_cast<const unsigned long long*>(d + X.o_acc), reinterpret_cast<const ModpFinal*>(d + X.o_fin),
-                batch, static_cast<uint32_t*>(out));
-            e = cudaGetLastError();
-        }
         if (e != cudaSuccess) return cuda_fail(e, "perm_modp launch");
         return PERMX_OK;
     }
     const bool cplx = X.field == Field::C128;
     const int pw = cplx ? 4 : 2;
-    const double* Ad = static_cast<const double*>(A);
-    if (X.x64) {
-        if (cplx)
-            stage_x64_kernel<2><<<(unsigned)batch, kStageX64Threads, 0, s>>>(
-                Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<int64_t*>(d + X.o_col));
-        else
-            stage_x64_kernel<1><<<(unsigned)batch, kStageX64Threads, 0, s>>>(
-                Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<int64_t*>(d + X.o_col));
-    } else if (cplx) {
-        stage_columns_kernel<double2><<<(unsigned)batch, 256, 0, s>>>(
-            reinterpret_cast<const double2*>(Ad), reinterpret_cast<const StageDesc*>(d + X.o_stage),
-            reinterpret_cast<double2*>(d + X.o_col));
-    } else {
-        stage_columns_kernel<double><<<(unsigned)batch, 256, 0, s>>>(
-            Ad, reinterpret_cast<const StageDesc*>(d + X.o_stage), reinterpret_cast<double*>(d + X.o_col));
-    }
-    e = cudaGetLastError();
+    const FpFinal* fin = reinterpret_cast<const FpFinal*>(d + X.o_fin);
+    const double* part = reinterpret_cast<const double*>(d + X.o_part);
     if (e == cudaSuccess)
         e = launch_groups(X, s, [&](const GroupPlan& g, cudaStream_t ls) {
             FpLaunch L;
@@ -779,15 +792,23 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
             L.ell = g.ell;
             L.log2_chunks = g.log2_chunks;
             L.nw = g.nw;
-            if (g.x64) return cplx ? dispatch_x64c(g.n, L, ls) : dispatch_x64r(g.n, L, ls);
-            return cplx ? dispatch_c128(g.n, L, ls) : dispatch_f64(g.n, L, ls);
+            const int64_t count = (int64_t)g.mats.size();
+            const bool fused = count <= kFuseFinalMax;
+            if (fused) {                        // the walk's last block finalises
+                L.fin = fin + g.first_mat;
+                L.nfin = (int)count;
+                L.cplx = cplx ? 1 : 0;
+                L.done = done + (&g - g0);
+                L.part_all = part;
+                L.out = out;
+            }
+            cudaError_t f;
+            if (g.x64) f = cplx ? dispatch_x64c(g.n, L, ls) : dispatch_x64r(g.n, L, ls);
+            else f = cplx ? dispatch_c128(g.n, L, ls) : dispatch_f64(g.n, L, ls);
+            if (f != cudaSuccess || fused) return f;
+            finalize_fp_kernel<<<(unsigned)count, kFinalThreads, 0, ls>>>(part, fin + g.first_mat, cplx ? 1 : 0, out);
+            return cudaGetLastError();
         });
-    if (e == cudaSuccess) {
-        finalize_fp_kernel<<<(unsigned)batch, kFinalThreads, 0, s>>>(
-            reinterpret_cast<const double*>(d + X.o_part), reinterpret_cast<const FpFinal*>(d + X.o_fin), cplx ? 1 : 0,
-            out);
-        e = cudaGetLastError();
-    }
     if (e != cudaSuccess) return cuda_fail(e, cplx ? "perm_c128 launch" : "perm_f64 launch");
     return PERMX_OK;
 }

@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include "common.cuh"
+
 namespace permx {
 
 enum class Field { C128 = 0, F64 = 1, MODP = 2 };
@@ -17,12 +19,6 @@ struct StageDesc {          // one matrix to stage column-major (offsets in entr
     int32_t nw;             // 1: also write x_i = a_{i,n-1} - (1/2) sum_j a_ij as column n
 };
 
-struct ModpFinal {
-    uint32_t p, rfix;       // rfix = 2^(32(n-1)) mod p undoes the Montgomery factors (times 2 in NW form)
-    int32_t negate;         // (-1)^n
-    int32_t pad_;
-    int64_t out_index;
-};
 
 struct ModpFinalAt {
     int64_t acc_index, out_index;
@@ -30,12 +26,6 @@ struct ModpFinalAt {
     int32_t negate, pad_;
 };
 
-struct FpFinal {
-    int64_t first, count;   // partial slots of this matrix
-    int64_t out_index;
-    int32_t negate;         // multiply by -1
-    int32_t twice;          // multiply by 2 (Nijenhuis-Wilf form)
-};
 
 struct GroupPlan {
     int n = 0, ell = 0, log2_chunks = 0, ld = 0, nw = 1;
@@ -82,7 +72,9 @@ struct Prepared {                   // a planned batch with its workspace (devic
     unsigned char* ws = nullptr;
     size_t bytes = 0;
     size_t o_stage = 0, o_p = 0, o_pinv = 0, o_fin = 0, o_meta_end = 0, o_acc = 0, o_col = 0, o_part = 0;
-    StreamSet* streams = nullptr;   // group streams (nullptr: this thread's set)
+    size_t o_done = 0, o_zero_end = 0;  // [o_done, o_zero_end): finalisation tickets (+ F_p accumulators), zeroed per execution
+    std::vector<unsigned char> meta;    // metadata passed by value to the set-up kernel (empty: uploaded once)
+    StreamSet* streams = nullptr;       // group streams (nullptr: this thread's set)
 };
 int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const uint32_t* p, int64_t batch,
                   cudaStream_t s, Prepared& X);

@@ -76,6 +76,26 @@ __device__ __forceinline__ int find_segment(const SegDesc* __restrict__ segs, in
 }
 #endif
 
+// Finalisation of one matrix (the fixed-order sum of its chunk partials).
+struct ModpFinal {
+    uint32_t p, rfix;       // rfix = 2^(32(n-1)) mod p undoes the Montgomery factors (times 2 in NW form)
+    int32_t negate;         // (-1)^n
+    int32_t pad_;
+    int64_t out_index;
+};
+struct FpFinal {
+    int64_t first, count;   // partial slots of this matrix
+    int64_t out_index;
+    int32_t negate;         // multiply by -1
+    int32_t twice;          // multiply by 2 (Nijenhuis-Wilf form)
+};
+
+// A walk launch of a group of at most kFuseFinalMax matrices finalises them in
+// its last block (the block that takes the last ticket of `done`), which
+// saves the finalisation launch of a lone matrix; the arithmetic is the
+// finalize kernels' own, so the bits are the same either way.
+constexpr int kFuseFinalMax = 4;
+
 struct ModpLaunch {
     const uint32_t* colT;          // group columns: matrix m at colT + m*mat_stride, column j at + j*pad4(n)
     const uint32_t* p;             // per-matrix prime
@@ -89,6 +109,12 @@ struct ModpLaunch {
     const SegDesc* segs = nullptr; // segment mode when non-null
     int nsegs = 0;
     int nw = 0;                    // 1: Nijenhuis-Wilf form (x column at index n)
+    // fused finalisation (batch mode, small groups): matrix m of the group has
+    // accumulator acc[m] and descriptor fin[m]; nullptr = a separate kernel
+    const ModpFinal* fin = nullptr;
+    int nfin = 0;
+    unsigned* done = nullptr;      // ticket counter, 0 before the launch, reset to 0 by the last block
+    uint32_t* out = nullptr;
 };
 
 struct FpLaunch {
@@ -101,13 +127,21 @@ struct FpLaunch {
     const SegDesc* segs = nullptr; // segment mode when non-null
     int nsegs = 0;
     int nw = 0;                    // 1: Nijenhuis-Wilf form (x column at index n)
+    // fused finalisation (batch mode, small groups): descriptors fin[0..nfin)
+    // index the whole batch's partial slots at part_all; nullptr = a separate kernel
+    const FpFinal* fin = nullptr;
+    int nfin = 0;
+    int cplx = 0;
+    unsigned* done = nullptr;      // ticket counter, 0 before the launch, reset to 0 by the last block
+    const double* part_all = nullptr;
+    void* out = nullptr;
 };
 
-template <int N> cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s);
-template <int N> cudaError_t launch_f64(const FpLaunch& L, int grid, cudaStream_t s);
-template <int N> cudaError_t launch_c128(const FpLaunch& L, int grid, cudaStream_t s);
-template <int N> cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s);
-template <int N> cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s);
+template <int N> cudaError_t launch_modp(const ModpLaunch& L, int grid, int threads, cudaStream_t s);
+template <int N> cudaError_t launch_f64(const FpLaunch& L, int grid, int threads, cudaStream_t s);
+template <int N> cudaError_t launch_c128(const FpLaunch& L, int grid, int threads, cudaStream_t s);
+template <int N> cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s);
+template <int N> cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s);
 template <int N> int blocks_per_sm_x64r();
 template <int N> int blocks_per_sm_x64c();
 template <int N> int blocks_per_sm_modp();

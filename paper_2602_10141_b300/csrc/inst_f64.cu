@@ -3,7 +3,7 @@
 
 namespace permx {
 #define PERMX_INST(N)                                                                  \
-    template cudaError_t launch_f64<N>(const FpLaunch&, int, cudaStream_t);            \
+    template cudaError_t launch_f64<N>(const FpLaunch&, int, int, cudaStream_t);            \
     template int blocks_per_sm_f64<N>();
 #include "inst_range.inc"
 }  // namespace permx

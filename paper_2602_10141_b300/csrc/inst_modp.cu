@@ -4,7 +4,7 @@
 
 namespace permx {
 #define PERMX_INST(N)                                                                  \
-    template cudaError_t launch_modp<N>(const ModpLaunch&, int, cudaStream_t);         \
+    template cudaError_t launch_modp<N>(const ModpLaunch&, int, int, cudaStream_t);         \
     template int blocks_per_sm_modp<N>();
 #include "inst_range.inc"
 }  // namespace permx

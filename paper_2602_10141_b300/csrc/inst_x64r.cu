@@ -3,7 +3,7 @@
 
 namespace permx {
 #define PERMX_INST(N)                                                                  \
-    template cudaError_t launch_x64r<N>(const FpLaunch&, int, cudaStream_t);           \
+    template cudaError_t launch_x64r<N>(const FpLaunch&, int, int, cudaStream_t);           \
     template int blocks_per_sm_x64r<N>();
 #include "inst_range.inc"
 }  // namespace permx

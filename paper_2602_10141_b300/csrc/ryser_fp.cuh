@@ -12,6 +12,7 @@
 // the slots of a matrix, which makes the result independent of scheduling.
 #pragma once
 #include "common.cuh"
+#include "finalize.cuh"
 
 namespace permx {
 
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_f64_kernel(const FpLau
         group_reduce(s, comp, G);
         if ((lane & (G - 1)) == 0 && valid) reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
     }
+    if (L.fin) fused_finalize_fp(L);
 }
 
 template <int N>
@@ -207,16 +209,17 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_c128_kernel(const FpLa
             out[1] = make_double2(si, ci);
         }
     }
+    if (L.fin) fused_finalize_fp(L);
 }
 
 template <int N>
-cudaError_t launch_f64(const FpLaunch& L, int grid, cudaStream_t s) {
-    ryser_f64_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+cudaError_t launch_f64(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    ryser_f64_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 template <int N>
-cudaError_t launch_c128(const FpLaunch& L, int grid, cudaStream_t s) {
-    ryser_c128_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+cudaError_t launch_c128(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    ryser_c128_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 template <int N>

@@ -20,6 +20,7 @@
 // int64 without reduction (L * 2^31 < 2^63) and reduced once per chunk.
 #pragma once
 #include "common.cuh"
+#include "finalize.cuh"
 
 namespace permx {
 
@@ -223,11 +224,12 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
         for (int d = 1; d < G; d <<= 1) part = mod_add(part, __shfl_xor_sync(0xffffffffu, part, d), p);
         if ((lane & (G - 1)) == 0 && valid && part) atomicAdd(acc, (unsigned long long)part);
     }
+    if (L.fin) fused_finalize_modp(L);
 }
 
 template <int N>
-cudaError_t launch_modp(const ModpLaunch& L, int grid, cudaStream_t s) {
-    ryser_modp_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+cudaError_t launch_modp(const ModpLaunch& L, int grid, int threads, cudaStream_t s) {
+    ryser_modp_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

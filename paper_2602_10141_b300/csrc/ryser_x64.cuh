@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
             reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
         }
     }
+    if (L.fin) fused_finalize_fp(L);
 }
 
 template <int N>
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
             out[1] = make_double2(si, ci);
         }
     }
+    if (L.fin) fused_finalize_fp(L);
 }
 
 // Complex rows wider than 16: two lanes share a chunk.  Lane h of a pair
@@ -362,17 +364,18 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
             out[1] = make_double2(si, ci);
         }
     }
+    if (L.fin) fused_finalize_fp(L);
 }
 
 template <int N>
-cudaError_t launch_x64r(const FpLaunch& L, int grid, cudaStream_t s) {
-    ryser_x64r_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    ryser_x64r_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 template <int N>
-cudaError_t launch_x64c(const FpLaunch& L, int grid, cudaStream_t s) {
-    if constexpr (x64c_paired(N)) ryser_x64c2_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
-    else ryser_x64c_kernel<N><<<grid, kRyserThreads, 0, s>>>(L);
+cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    if constexpr (x64c_paired(N)) ryser_x64c2_kernel<N><<<grid, threads, 0, s>>>(L);
+    else ryser_x64c_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 template <int N>

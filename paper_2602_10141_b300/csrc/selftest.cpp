@@ -16,6 +16,8 @@ extern "C" {
 
 int64_t permx_x64_mulhi62(int64_t a, int64_t b) { return x64_mulhi62(a, b); }
 
+int64_t permx_x64_scaled_round(double a, int32_t k) { return x64_scaled_round(a, k); }
+
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {
     if (!R || !m_out || !e_out || n < 1 || n > 64) return -1;
     XReal t[4];

@@ -70,6 +70,36 @@ __host__ __device__ __forceinline__ int64_t x64_shl(int64_t x, int s) {
     return (int64_t)(((uint64_t)nhi << 32) | (uint32_t)(lo << s));
 }
 
+// round(a 2^k) to the nearest integer, ties to even, for a finite double a
+// with |a 2^k| < 2^62 (how staging turns an entry into the walk's integer):
+// integer operations on a's sign, exponent and 53-bit significand, with one
+// rounding (llrint(ldexp(a, k)) rounds twice when ldexp lands in the
+// subnormal range).
+__host__ __device__ __forceinline__ int64_t x64_scaled_round(double a, int k) {
+#ifdef __CUDA_ARCH__
+    const uint64_t bits = (uint64_t)__double_as_longlong(a);
+#else
+    uint64_t bits;
+    __builtin_memcpy(&bits, &a, sizeof bits);
+#endif
+    const int be = (int)((bits >> 52) & 0x7ff);
+    const uint64_t frac = bits & ((1ull << 52) - 1);
+    const uint64_t m = be ? (frac | (1ull << 52)) : frac;      // |a| = m 2^(be - 1075), or m 2^-1074 if subnormal
+    const int sh = (be ? be : 1) - 1075 + k;                     // |a| 2^k = m 2^sh
+    uint64_t q;
+    if (sh >= 0) {
+        q = m << sh;                                            // < 2^62 by the caller's bound
+    } else if (sh >= -53) {
+        const int d = -sh;
+        q = m >> d;
+        const uint64_t rem = m & ((1ull << d) - 1), half = 1ull << (d - 1);
+        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+    } else {
+        q = 0;                                                  // |a| 2^k < 1/2
+    }
+    return (bits >> 63) ? -(int64_t)q : (int64_t)q;
+}
+
 struct XReal { int64_t m; int e; };
 struct XCplx { int64_t re, im; int e; };
 

@@ -245,6 +245,9 @@ def test_binding_rejects_tensors_on_another_device(px, monkeypatch):
         def device(self):
             return torch.device("cuda", self._dev)
 
+        def get_device(self):
+            return self._dev
+
     def on(t, dev):
         f = t.as_subclass(FakeCuda)
         f._dev = dev

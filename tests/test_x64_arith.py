@@ -172,3 +172,29 @@ def test_accumulator_merge_exact_and_symmetric(lib, parts):
         tot = sum(Fraction(abs(mm)) * Fraction(2) ** (ee - base) for mm, ee in zip(m, e))
         got = Fraction(outs[0][0]) + Fraction(outs[0][1])
         assert abs(got - exact) <= tot * Fraction(1, 2 ** 70) + abs(exact) * Fraction(1, 2 ** 100)
+
+
+def test_scaled_round_is_exact_round_half_even(lib):
+    """Staging's float -> integer conversion rounds a 2^k once, to nearest with
+    ties to even, for normal and subnormal a and both signs, checked against
+    exact rational arithmetic."""
+    import math
+    from fractions import Fraction
+    f = lib.permx_x64_scaled_round
+    f.argtypes = [ctypes.c_double, ctypes.c_int32]
+    f.restype = ctypes.c_int64
+    rnd = random.Random(11)
+    vals = [0.0, -0.0, 1.0, -1.0, 0.5, 1.5, 2.5, -2.5, 3.5, 5e-324, -5e-324, 2.2250738585072014e-308,
+            1.7976931348623157e308, math.ldexp(1.0, -1074) * 3]
+    vals += [rnd.uniform(-1, 1) * 10 ** rnd.uniform(-300, 300) for _ in range(3000)]
+    vals += [math.ldexp(rnd.randint(1, 2 ** 53) + 0.5, rnd.randint(-60, 0)) for _ in range(500)]   # exact ties
+    for a in vals:
+        e = math.frexp(a)[1] if a else 0
+        for k in (60 - e, 59 - e, 40 - e, 1 - e, -e, -e - 1, -e - 60, 61 - e):
+            x = Fraction(a) * Fraction(2) ** k
+            if abs(x) >= 2 ** 62:
+                continue
+            fl = math.floor(x)
+            d = x - fl
+            want = fl + 1 if d > Fraction(1, 2) or (d == Fraction(1, 2) and fl % 2) else fl
+            assert f(a, k) == want, (a, k)
