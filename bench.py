@@ -41,12 +41,13 @@ NPRIMES = 5
 METRIC = "ryser_terms_per_s"
 UNIT = "terms/s"
 WORKLOAD = "schur_n33_fp_5primes"
-# dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch over the
-# 2^30-step small case (bench.py --profile-case, one ncu pass), scaled by the steps of a
-# bench launch (5 x 2^32): the traffic is the residue tables and instruction fetch, and
-# grows with the launch's length; see profiles/ryser_modp_n33_schur.md
-WALK_DRAM_BYTES_SMALL_CASE = 36_000
-WALK_DRAM_BYTES_PER_LAUNCH = WALK_DRAM_BYTES_SMALL_CASE * (NPRIMES * 2 ** 32) // 2 ** 30
+# dram__bytes_read.sum + dram__bytes_write.sum of one ryser_modp_kernel<33> launch of the
+# small case (bench.py --profile-case: 2^30 Gray steps of S_33 mod p, the same kernel), from
+# one ncu capture of the current build; not scaled to the bench launch (5 x 2^32 steps): the
+# walk reads its residue tables once and otherwise only instruction fetch reaches DRAM, which
+# grows far slower than the launch (0.96 MB measured once at full size); see
+# profiles/ryser_modp_n33_schur.md
+WALK_DRAM_BYTES_SMALL_CASE = 402_432
 
 
 def _rank_env():
@@ -432,8 +433,9 @@ def main():
             "perms_per_s": NPRIMES * args.steps * world / t_max,
             "terms_evaluated_per_s": evaluated_per_step * args.steps * world / t_max,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tterms/s",
-                         "frac": achieved / peak, "traffic": WALK_DRAM_BYTES_PER_LAUNCH,
-                         "traffic_unit": "bytes per launch (small-case capture scaled to the launch)",
+                         "frac": achieved / peak, "traffic": WALK_DRAM_BYTES_SMALL_CASE,
+                         "traffic_unit": "bytes per launch of the 2^30-step small case of the same kernel "
+                                         "(ncu, current build; residue tables + instruction fetch, not scaled)",
                          "kernel": f"ryser_modp_kernel<{N}>",
                          "peak_source": "integer-multiply-pipe bound 1/(1/R_wide + 1/R_lo + 1/R_hi) from the "
                                         "library's issue-rate probes run in this process (permx_peak_probe)",

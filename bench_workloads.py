@@ -68,12 +68,54 @@ def run(args):
     raise ValueError(args.workload)
 
 
+def schur_strong_split(args, world: int) -> int:
+    """Config 5 under torchrun (N > 1): every perm(S_n) split over the N GPUs
+    (paper_2602_10141_b300.sharding: ranges of every prime's Gray walk
+    round-robin over the ranks, one all_gather of a residue per prime, CRT
+    once); rank 0 prints one JSON line per n with the time of the whole split."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_10141_b300 as px
+    from paper_2602_10141_b300.sharding import schur_strong
+    from bench import ClockSampler
+    rank, local = int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    ns = [int(x) for x in args.ns.split(",")] if args.ns else list(range(36, 44))
+    for n in ns:
+        k = px.perm_schur_prime_count(n)
+        primes = px.perm_primes_1_mod_n(n, k + 1)
+        slices = max(1, -(-4 * world // len(primes)))        # several ranges per rank
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            value, residues = schur_strong(n, primes, slices)
+        dt = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+        if rank == 0:
+            terms = len(primes) * n * 2.0 ** (n - 1)
+            print(json.dumps({"workload": "schur_long", "n": n, "perm_S_n": str(value), "seconds": float(dt.item()),
+                              "n_gpus": world, "scaling": "strong", "slices_per_prime": slices, "primes": primes,
+                              "residues": residues, "check_prime": primes[-1],
+                              "evaluated_terms_per_s": terms / float(dt.item()), "clocks_rank0": clk.summary(),
+                              "bound_ok": value * value <= n ** n}), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def schur_long(args):
     """Exact perm(S_n) for n = 36..43 by default (any n <= 48 with --ns; 5 or 6
     primes below 2^31 + 1 check prime each), sliced into checkpointed kernel
     launches; one JSON line per n.  With --ckpt-dir and --max-slices a long n
-    runs over several invocations, each resuming from the checkpoint."""
+    runs over several invocations, each resuming from the checkpoint.  Under
+    torchrun with N > 1 ranks each n is split over the N GPUs instead
+    (schur_strong_split)."""
     import tempfile
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return schur_strong_split(args, world)
 
     import paper_2602_10141_b300 as px
     import oracle as O

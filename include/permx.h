@@ -299,6 +299,25 @@ int perm_schur_crt_primes(int32_t n, const uint32_t* primes, int32_t count, cons
                           uint64_t slice_subsets, int64_t max_slices, int64_t out_i128[2], char* out_dec,
                           size_t out_dec_len, uint32_t* residues_out);
 
+/* One shard of perm(S_n) for a strong split over several GPUs or processes
+ * (paper §2.1 CRT method, §2.2 Gray-code blocks: the blocks of every prime
+ * are independent, so any set of them can run anywhere and only their sums
+ * are exchanged).  The Nijenhuis-Wilf walk of 2^(n-1) Gray indices of every
+ * prime primes[i] (i < count) is cut into `slices` equal ranges; work item
+ * w = i * slices + j (prime i, range j) belongs to shard w mod nshards.
+ * partial_out[i] (host, count entries) receives this shard's signed sum over
+ * its ranges of prime i, mod primes[i], without the walk's factor
+ * 2 (-1)^(n-1); 0 where the shard has no range of prime i.  Combining: add
+ * the shards' partial_out[i] mod primes[i], multiply by 2 (-1)^(n-1) to get
+ * perm(S_n) mod primes[i], then reconstruct with perm_crt (use one prime more
+ * than the bound needs as a check).  Synchronous, on the current device; the
+ * residue matrices are built on the host as in perm_schur_crt.
+ * 1 <= n <= PERMX_MAX_N_MODP, 1 <= count <= PERMX_MAX_PRIMES, every prime an
+ * odd prime below 2^31 with p = 1 (mod n), slices >= 1, 0 <= shard < nshards.
+ * Errors: EINVAL (before any GPU work), ENOMEM, ECUDA. */
+int perm_schur_shard(int32_t n, const uint32_t* primes, int32_t count, int32_t slices, int32_t shard,
+                     int32_t nshards, uint32_t* partial_out);
+
 /* ------------------------------------------------------------------------
  * Host-side field and CRT helpers (paper §2.1); no GPU needed.
  * ---------------------------------------------------------------------- */

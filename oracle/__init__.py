@@ -296,6 +296,34 @@ def is_prime(m: int) -> bool:
     return True
 
 
+def ryser_nw_modp_gray_range(A, p: int, k0: int, k1: int) -> int:
+    """The Nijenhuis-Wilf form of Ryser's sum over Gray indices [k0, k1) of its
+    2^(n-1)-subset walk, mod p (pure Python, small n):
+
+        sum_{k0<=k<k1} (-1)^{|g(k)|} prod_i (x_i + sum_{j in g(k)} a_ij),
+        x_i = a_{i,n-1} - (1/2) sum_j a_ij,  1/2 = (p+1)/2 mod p,
+
+    with g(k) = k ^ (k >> 1) a subset of the columns 0..n-2 and every row sum
+    recomputed for every subset.  No (-1)^(n-1) 2 factor: over the whole range
+    [0, 2^(n-1)) it equals (-1)^(n-1) perm(A) / 2 mod p (p odd).
+    """
+    a = [[int(v) % p for v in row] for row in np.asarray(A)]
+    n = len(a)
+    if n < 1 or not 0 <= k0 <= k1 <= 1 << (n - 1):
+        raise ValueError("need n >= 1 and 0 <= k0 <= k1 <= 2^(n-1)")
+    half = (p + 1) // 2
+    x = [(a[i][n - 1] - half * sum(a[i])) % p for i in range(n)]
+    total = 0
+    for k in range(k0, k1):
+        S = k ^ (k >> 1)
+        cols = [j for j in range(n - 1) if S >> j & 1]
+        prod = 1
+        for i in range(n):
+            prod = prod * ((x[i] + sum(a[i][j] for j in cols)) % p) % p
+        total = (total - prod) % p if len(cols) & 1 else (total + prod) % p
+    return total
+
+
 def primes_1_mod_n(n: int, count: int, below: int = 2 ** 31, skip: int = 0) -> list[int]:
     """The largest primes p < ``below`` with p = 1 (mod n), in descending order.
 

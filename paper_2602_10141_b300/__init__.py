@@ -69,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "perm_schur_residues": ([i32, u32, u32, P(u32)], ctypes.c_int),
         "perm_crt": ([P(u32), P(u32), i32, P(i64)], ctypes.c_int),
         "perm_schur_prime_count": ([i32], ctypes.c_int),
+        "perm_schur_shard": ([i32, P(u32), i32, i32, i32, i32, P(u32)], ctypes.c_int),
         "permx_set_fp_arith": ([ctypes.c_int], ctypes.c_int),
         "perm_plan_create": ([ctypes.c_int, P(i32), P(i64), P(u32), i64, vp, P(vp)], ctypes.c_int),
         "perm_plan_execute": ([vp, vp, vp, vp], ctypes.c_int),
@@ -626,6 +627,16 @@ def perm_schur_crt_primes(n: int, primes, ckpt_path: str | None = None, slice_su
                                       ckpt_path.encode() if ckpt_path else None, slice_subsets, max_slices, None,
                                       buf, len(buf), _p(res, ctypes.c_uint32)))
     return int(buf.value.decode()), [int(x) for x in res]
+
+
+def perm_schur_shard(n: int, primes, slices: int, shard: int, nshards: int) -> list[int]:
+    """One shard's partial sums of perm(S_n) on the current GPU (see
+    perm_schur_shard in include/permx.h and sharding.py)."""
+    pp = _u32(primes)
+    out = np.zeros(len(pp), np.uint32)
+    _check(_lib.perm_schur_shard(n, _p(pp, ctypes.c_uint32), len(pp), slices, shard, nshards,
+                                 _p(out, ctypes.c_uint32)))
+    return [int(x) for x in out]
 
 
 def perm_primes_1_mod_n(n: int, count: int, skip: int = 0) -> list[int]:

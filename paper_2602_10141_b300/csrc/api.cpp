@@ -195,6 +195,17 @@ int perm_schur_crt_primes(int32_t n, const uint32_t* primes, int32_t count, cons
     return schur_outputs(rc, res, out_i128, out_dec, out_dec_len, residues_out, nullptr);
 }
 
+int perm_schur_shard(int32_t n, const uint32_t* primes, int32_t count, int32_t slices, int32_t shard, int32_t nshards,
+                     uint32_t* partial_out) {
+    clear_error();
+    if (!primes || !partial_out || count < 1 || count > PERMX_MAX_PRIMES) return fail(PERMX_EINVAL, "bad arguments");
+    std::vector<uint32_t> part;
+    const int rc = schur_shard(n, std::vector<uint32_t>(primes, primes + count), slices, shard, nshards, part);
+    if (rc) return rc;
+    for (int32_t i = 0; i < count; ++i) partial_out[i] = part[(size_t)i];
+    return PERMX_OK;
+}
+
 int perm_schur_crt_ex(int32_t n, int32_t nprimes, const char* ckpt_path, uint64_t slice_subsets, int64_t max_slices,
                       int64_t out_i128[2], char* out_dec, size_t out_dec_len, uint32_t* residues_out,
                       uint32_t* primes_out) {

@@ -310,4 +310,61 @@ int schur_crt_run_primes(int n, const std::vector<uint32_t>& primes, const char*
     return PERMX_OK;
 }
 
+// One shard of a strong split of perm(S_n) over several GPUs: the
+// Nijenhuis-Wilf walk of every prime is cut into `slices` equal Gray ranges;
+// work item w = i * slices + j (prime i, range j) belongs to shard w mod
+// nshards.  partial[i] = this shard's signed sum over its ranges of prime i
+// mod p_i (0 if it has none), without the factor 2 (-1)^(n-1).
+int schur_shard(int n, const std::vector<uint32_t>& primes, int slices, int shard, int nshards,
+                std::vector<uint32_t>& partial) {
+    if (n < 1 || n > PERMX_MAX_N_MODP) return fail(PERMX_EINVAL, "n outside [1, 48]");
+    if (primes.empty() || primes.size() > (size_t)PERMX_MAX_PRIMES) return fail(PERMX_EINVAL, "need 1..64 primes");
+    if (slices < 1 || nshards < 1 || shard < 0 || shard >= nshards)
+        return fail(PERMX_EINVAL, "need slices >= 1 and 0 <= shard < nshards");
+    for (size_t i = 0; i < primes.size(); ++i) {
+        const uint32_t p = primes[i];
+        if (p <= 2 || p >= (1u << 31) || !is_prime_u32(p) || p % (uint32_t)n != 1 % (uint32_t)n)
+            return fail(PERMX_EINVAL, "prime " + std::to_string(p) + " is not an odd prime below 2^31 with p = 1 (mod n)");
+    }
+    const uint64_t total = 1ull << walk_bits(n, 1);
+    const uint64_t len = (total + (uint64_t)slices - 1) / (uint64_t)slices;
+    partial.assign(primes.size(), 0);
+    cudaStream_t s;
+    PERMX_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    uint32_t* dA = nullptr;
+    cudaError_t e = ws_alloc(reinterpret_cast<void**>(&dA), sizeof(uint32_t) * n * n, s);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    std::vector<uint32_t> hA((size_t)n * n);
+    int rc = PERMX_OK;
+    for (size_t i = 0; i < primes.size() && rc == PERMX_OK; ++i) {
+        std::vector<uint64_t> mine;
+        for (int j = 0; j < slices; ++j)
+            if (((uint64_t)i * (uint64_t)slices + (uint64_t)j) % (uint64_t)nshards == (uint64_t)shard) mine.push_back(j);
+        if (mine.empty()) continue;
+        const uint32_t p = primes[i];
+        uint32_t g = 0;
+        if (primitive_root(p, n, &g) != 0) { rc = fail(PERMX_EINVAL, "no primitive root"); break; }
+        schur_residues(n, p, g, hA.data());
+        e = cudaMemcpyAsync(dA, hA.data(), sizeof(uint32_t) * n * n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync"); break; }
+        ModpRange R;
+        rc = R.init(dA, n, p, 1, s, len);
+        for (size_t q = 0; q < mine.size() && rc == PERMX_OK; ++q) {
+            const uint64_t k0 = mine[q] * len, k1 = k0 + len < total ? k0 + len : total;
+            if (k0 >= k1) continue;
+            uint32_t part = 0;
+            rc = R.run(k0, k1, &part);
+            if (rc == PERMX_OK) partial[i] = (uint32_t)(((uint64_t)partial[i] + part) % p);
+        }
+        R.release();
+    }
+    ws_free(dA, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return rc;
+}
+
 }  // namespace permx

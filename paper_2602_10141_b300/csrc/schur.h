@@ -54,4 +54,8 @@ int schur_crt_run(int n, int nprimes, const char* ckpt_path, uint64_t slice_subs
 int schur_crt_run_primes(int n, const std::vector<uint32_t>& primes, const char* ckpt_path, uint64_t slice_subsets,
                          int64_t max_slices, SchurResult& res);
 
+// one shard of a strong split over GPUs (see perm_schur_shard)
+int schur_shard(int n, const std::vector<uint32_t>& primes, int slices, int shard, int nshards,
+                std::vector<uint32_t>& partial);
+
 }  // namespace permx

@@ -185,3 +185,21 @@ def test_schur_crt_fixture_consistent():
             q = O.primes_1_mod_n(n, 1, below=min(used))[0]     # the next prime down, unused
             S = O.schur_residue_matrix(n, q, O.primitive_nth_root(q, n))
             assert value % q == O.perm_modp(S, q), n
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_nw_range_sum_gives_perm_by_brute_force(n):
+    """Nijenhuis-Wilf form: (-1)^(n-1) 2 times the sum over all 2^(n-1) Gray
+    indices is perm(A) mod p (brute force over the n! permutations); sums over
+    the pieces of a partition of the range add up to the whole."""
+    g = rng(6000 + n)
+    for p in (3, 7, 2147483629):
+        A = random_residues(n, p, g)
+        full = O.ryser_nw_modp_gray_range(A, p, 0, 1 << (n - 1))
+        v = full * 2 % p
+        if (n - 1) % 2:
+            v = (p - v) % p
+        assert v == O.perm_modp_brute(A, p), (n, p)
+        cuts = sorted({0, 1 << (n - 1)} | {int(c) for c in g.integers(0, (1 << (n - 1)) + 1, size=3)})
+        parts = sum(O.ryser_nw_modp_gray_range(A, p, a, b) for a, b in zip(cuts, cuts[1:])) % p
+        assert parts == full
