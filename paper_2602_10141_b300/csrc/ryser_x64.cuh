@@ -367,6 +367,176 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
     if (L.fin) fused_finalize_fp(L);
 }
 
+// Four lanes per chunk (complex, 8 <= n <= 16), for launches too small to
+// give every SM sub-partition a warp of the one-lane kernel (a lone matrix, a
+// small serving step).  Lane q of a quad owns rows i = q (mod 4) of its chunk,
+// keeps their row sums and forms product chain q exactly as the one-lane
+// kernel does (R_q, then times R_{q+4}, R_{q+8}, ...); the quad exchanges its
+// four chains and every lane combines them in the one-lane kernel's order
+// ((t0 t1)(t2 t3)) and adds the term to its (identical) chunk accumulators.
+// A block of four warps holds 32 consecutive chunks, so the lane groups'
+// merge tree is the one-lane kernel's: levels of chunk distance 1, 2, 4
+// between lanes 4, 8, 16 apart, levels 8 and 16 between warps through shared
+// memory.  Every result bit equals the one-lane kernel's.
+constexpr int kQuadThreads = 128;
+template <int N> constexpr bool x64c_quad_ok() { return N >= 8 && N <= 16 && !x64c_paired(N); }
+
+__device__ __forceinline__ void xacc_store(long long* d, const XAcc& a) {
+    d[0] = (long long)(unsigned long long)(uint64_t)a.acc;
+    d[1] = (long long)(uint64_t)((unsigned __int128)a.acc >> 64);
+    d[2] = a.E;
+    d[3] = a.set;
+}
+__device__ __forceinline__ XAcc xacc_load(const long long* d) {
+    XAcc a;
+    a.acc = (__int128)(((unsigned __int128)(uint64_t)d[1] << 64) | (uint64_t)d[0]);
+    a.E = (int)d[2];
+    a.set = d[3] != 0;
+    return a;
+}
+__device__ __forceinline__ XCplx shfl_cplx(unsigned mask, const XCplx& t, int src) {
+    XCplx o;
+    o.re = (int64_t)__shfl_sync(mask, (long long)t.re, src);
+    o.im = (int64_t)__shfl_sync(mask, (long long)t.im, src);
+    o.e = __shfl_sync(mask, t.e, src);
+    return o;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunch L) {
+    static_assert(N >= 8 && N <= 16, "the four-lane walk covers 8 <= n <= 16");
+    constexpr int RQ = (N + 3) / 4;                 // rows of lane 0 (lanes with q >= N % 4 may own one fewer)
+    __shared__ long long sh[4][2][4];               // per warp: (re, im) accumulators for the cross-warp levels
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 3;
+    const int cl = 8 * w + (lane >> 2);             // chunk within the block's 32
+    const unsigned quad = 0xFu << (lane & ~3);
+    const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    const int lg = L.log2_chunks >= 5 ? 5 : L.log2_chunks;
+    const int G = 1 << lg;
+    for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * 32; base < L.item_end;
+         base += (uint64_t)gridDim.x * 32) {
+        const uint64_t item = base + cl;
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        bool valid = item < L.item_end;
+        const double* cold = L.colT;
+        uint64_t c = 0, slot = 0;
+        XAcc ar, ai;
+        x64_acc_init(ar);
+        x64_acc_init(ai);
+        int scale = 0;
+        bool nonfinite = false;
+        if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
+        if (valid) {
+            const longlong2* col = reinterpret_cast<const longlong2*>(cold);
+            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            int64_t Rr[RQ], Ri[RQ];
+#pragma unroll
+            for (int k = 0; k < RQ; ++k) {
+                Rr[k] = 0;
+                Ri[k] = 0;
+                if (q + 4 * k < N) {
+                    const longlong2 x = __ldg(col + N * N + q + 4 * k);
+                    Rr[k] = x.x;
+                    Ri[k] = x.y;
+                }
+            }
+            const uint64_t S0 = ks ^ (ks >> 1);
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                if (!((S0 >> j) & 1)) continue;
+#pragma unroll
+                for (int k = 0; k < RQ; ++k) {
+                    if (q + 4 * k < N) {
+                        const longlong2 v = __ldg(col + j * N + q + 4 * k);
+                        Rr[k] += v.x;
+                        Ri[k] += v.y;
+                    }
+                }
+            }
+            scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
+            nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
+            for (uint64_t k = ks; k < ke; ++k) {
+                if (k > ks) {
+                    const int j = __ffsll((long long)k) - 1;
+                    const longlong2* cj = col + j * N + q;
+                    if ((k >> (j + 1)) & 1) {
+#pragma unroll
+                        for (int r = 0; r < RQ; ++r) {
+                            if (q + 4 * r < N) {
+                                const longlong2 v = __ldg(cj + 4 * r);
+                                Rr[r] -= v.x;
+                                Ri[r] -= v.y;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RQ; ++r) {
+                            if (q + 4 * r < N) {
+                                const longlong2 v = __ldg(cj + 4 * r);
+                                Rr[r] += v.x;
+                                Ri[r] += v.y;
+                            }
+                        }
+                    }
+                }
+                // chain q (rows q, q+4, q+8, ...), as the one-lane kernel forms t[q]
+                XCplx t = x64c_from_int(Rr[0], Ri[0]);
+#pragma unroll
+                for (int r = 1; r < RQ; ++r)
+                    if (q + 4 * r < N) t = x64c_mul(t, Rr[r], Ri[r], 0);
+                const int q0 = lane & ~3;
+                const XCplx t0 = shfl_cplx(quad, t, q0), t1 = shfl_cplx(quad, t, q0 + 1);
+                const XCplx t2 = shfl_cplx(quad, t, q0 + 2), t3 = shfl_cplx(quad, t, q0 + 3);
+                XCplx pr = x64c_mul(t0, t1.re, t1.im, t1.e);
+                const XCplx p23 = x64c_mul(t2, t3.re, t3.im, t3.e);
+                pr = x64c_mul(pr, p23.re, p23.im, p23.e);
+                x64_acc_add(ar, pr.re, pr.e, k & 1);
+                x64_acc_add(ai, pr.im, pr.e, k & 1);
+            }
+        }
+        // the lane groups' merge tree over chunks: distances 1, 2, 4 inside the warp
+        for (int d = 1; d < G && d < 8; d <<= 1) {
+            XAcc b;
+            const uint64_t lo = (uint64_t)ar.acc, hi = (uint64_t)(ar.acc >> 64);
+            b.acc = (__int128)(((unsigned __int128)(uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)hi, 4 * d)
+                                << 64) |
+                               (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo, 4 * d));
+            b.E = __shfl_xor_sync(0xffffffffu, ar.E, 4 * d);
+            b.set = __shfl_xor_sync(0xffffffffu, (int)ar.set, 4 * d) != 0;
+            x64_acc_merge(ar, b);
+            const uint64_t lo2 = (uint64_t)ai.acc, hi2 = (uint64_t)(ai.acc >> 64);
+            b.acc = (__int128)(((unsigned __int128)(uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)hi2, 4 * d)
+                                << 64) |
+                               (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)lo2, 4 * d));
+            b.E = __shfl_xor_sync(0xffffffffu, ai.E, 4 * d);
+            b.set = __shfl_xor_sync(0xffffffffu, (int)ai.set, 4 * d) != 0;
+            x64_acc_merge(ai, b);
+        }
+        // distances 8 and 16 between warps (every lane of a warp holds its warp's subtree)
+        for (int d = 8; d < G; d <<= 1) {
+            if (lane == 0) {
+                xacc_store(sh[w][0], ar);
+                xacc_store(sh[w][1], ai);
+            }
+            __syncthreads();
+            const int pw = w ^ (d >> 3);
+            const XAcc br = xacc_load(sh[pw][0]), bi = xacc_load(sh[pw][1]);
+            __syncthreads();
+            x64_acc_merge(ar, br);
+            x64_acc_merge(ai, bi);
+        }
+        if (q == 0 && (cl & (G - 1)) == 0 && valid) {
+            x64_acc_to_dd(ar, scale, sr, cr);
+            x64_acc_to_dd(ai, scale, si, ci);
+            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
+            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
+            out[0] = make_double2(sr, cr);
+            out[1] = make_double2(si, ci);
+        }
+    }
+    if (L.fin) fused_finalize_fp(L);
+}
+
 template <int N>
 cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
     ryser_x64r_kernel<N><<<grid, threads, 0, s>>>(L);
@@ -374,6 +544,14 @@ cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s
 }
 template <int N>
 cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    if constexpr (x64c_quad_ok<N>()) {
+        // fewer one-lane warps than SM sub-partitions: four lanes per chunk (same bits)
+        const uint64_t items = L.item_end - L.item_begin;
+        if (items < (uint64_t)sm_count() * 128) {
+            ryser_x64c4_kernel<N><<<(unsigned)((items + 31) / 32), kQuadThreads, 0, s>>>(L);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (x64c_paired(N)) ryser_x64c2_kernel<N><<<grid, threads, 0, s>>>(L);
     else ryser_x64c_kernel<N><<<grid, threads, 0, s>>>(L);
     return cudaGetLastError();

@@ -421,3 +421,30 @@ def test_schur33_benchmark_launch_matches_oracle_residue(px):
     mats = [O.schur_residue_matrix(n, q, O.primitive_nth_root(q, n)) for q in primes]
     got = run_modp(px, mats, primes)
     assert int(got[0]) == r
+
+
+@pytest.mark.parametrize("n", [8, 9, 12, 14, 15, 16])
+def test_lone_complex_walk_equals_batched_bits(px, n):
+    """Integer mode: a lone complex matrix runs four lanes per chunk, the same
+    matrix in a batch large enough for the one-lane walk runs one; the bits
+    agree, with the built-in chunking (lane groups of 16 or 32 chunks, merged
+    across warps) and with a pinned chunk length that leaves groups of 4."""
+    import torch
+    old = px.permx_set_fp_arith(px.FP_ARITH_INT)
+    saved = px.perm_tune_get(px.FIELD_C128, n)
+    try:
+        A = ensemble("haar_u", n, 1, seed=8000 + n)[0]
+        for ell in (0, n - 3):                    # 0: the built-in rule
+            px.perm_tune_set(px.FIELD_C128, n, ell)
+            chunks = 2 ** (n - 1 - px.perm_tune_get(px.FIELD_C128, n))
+            others = list(ensemble("ginibre_c", n, -(-20000 // chunks) + 1, seed=8100 + n))
+            lone = run_fp(px, [A])[0]
+            both = run_fp(px, others[:3] + [A] + others[3:])
+            assert both[3] == lone, (n, ell)
+            ref = O.perm_dp(A)
+            assert abs(lone - ref) <= 1e-9 * abs(ref)
+        torch.cuda.synchronize()
+    finally:
+        px.perm_tune_set(px.FIELD_C128, n, 0)
+        assert px.perm_tune_get(px.FIELD_C128, n) == saved
+        px.permx_set_fp_arith(old)
