@@ -669,9 +669,10 @@ def _request_mix(count: int, seed: int):
 
 def _drive(S, reqs, arrivals):
     """Submit at the given arrival times (s), poll until all done; returns
-    latencies (measured inside the library), makespan and results."""
+    latencies (measured inside the library, in request order), makespan and
+    results."""
     pending = {}
-    lat = []
+    lat = [0.0] * len(reqs)
     results = [None] * len(reqs)
     t0 = time.perf_counter()
     i = 0
@@ -685,7 +686,7 @@ def _drive(S, reqs, arrivals):
             r = S.poll(tk)
             if r is not None:
                 results[pending[tk]] = r[0]
-                lat.append(r[1])
+                lat[pending[tk]] = r[1]
                 del pending[tk]
         if i < len(reqs) and not pending:
             time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.001)))
@@ -727,8 +728,18 @@ def served_object(scale: float = 1.0, work_budget: int = 0) -> dict:
             st = S.stats()
             S.close()
             lat = np.array(lat)
+            kinds = np.array([("c128" if f == 0 else "f64" if f == 1 else "modp") for _, f, _ in reqs])
+            sizes = np.array([A.shape[0] for A, _, _ in reqs])
+            by_field = {k: {"p50_ms": float(np.percentile(lat[kinds == k], 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat[kinds == k], 99) * 1e3),
+                            "requests": int((kinds == k).sum())} for k in ("c128", "f64", "modp")}
+            tail = lat >= np.percentile(lat, 99)
             out[name] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
                          "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                         "by_field": by_field,
+                         "p99_tail": {"requests": int(tail.sum()),
+                                      "fields": {k: int((tail & (kinds == k)).sum()) for k in ("c128", "f64", "modp")},
+                                      "mean_n": float(sizes[tail].mean())},
                          "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
                          "throughput_rps": count / span, "makespan_s": span, "steps": st["steps"],
                          "launches": st["launches"], "gpu_busy_ms": st["gpu_busy_ms"],

@@ -224,11 +224,15 @@ int enqueue_step(perm_server* S, StepBuf& B, int slot, const std::vector<Request
     cudaStream_t st = S->stream;
     B.results.clear();
     // ---- grants -------------------------------------------------------------------------
-    // A chunk is one thread's Gray walk.  Per step every (field, n) class may
-    // run one wave of its kernel's resident threads (classes run concurrently
-    // on the side streams), or chunks_per_step chunks in total when set.
-    // Within a class every request first gets a fair share (at least one lane
-    // group), then the rest of the wave goes to the oldest requests first.
+    // A chunk is one thread's Gray walk; a wave is one chunk for every
+    // resident thread of the class kernel.  The class kernels of a step share
+    // the SMs one after another, so a step lasts about the sum of their wave
+    // times, and a class with short chunks would progress one short wave per
+    // long step.  Per step every (field, n) class therefore gets as many
+    // waves as fit in the longest single-wave time of the step (at most 16),
+    // or chunks_per_step chunks in total when set.  Within a class every
+    // request first gets a fair share (at least one lane group), then the
+    // rest goes to the oldest requests first.
     std::vector<Request*> act;
     for (Request* r : S->resident)
         if (r->next_chunk < r->chunks) act.push_back(r);   // admission order
@@ -236,13 +240,21 @@ int enqueue_step(perm_server* S, StepBuf& B, int slot, const std::vector<Request
     std::map<std::pair<int, int>, std::vector<size_t>> by_class;
     for (size_t i = 0; i < act.size(); ++i) by_class[{act[i]->field, act[i]->n}].push_back(i);
     const int64_t fixed = S->cfg.chunks_per_step;
+    // one chunk's time on its lane(s), in complex128-term units: 2^ell steps of n terms
+    auto chunk_time = [](const Request* r) {
+        const int lanes = chunks_per_warp(r->x64, r->field == PERMX_FIELD_C128, r->n) == 16 ? 2 : 1;
+        return std::ldexp(1.0, r->ell) * r->n * term_cost(r->field, r->x64) / lanes;
+    };
+    double longest = 0.0;
+    for (auto& kv : by_class) longest = std::max(longest, chunk_time(act[kv.second[0]]));
     for (auto& kv : by_class) {
         const std::vector<size_t>& idx = kv.second;
         Request* r0 = act[idx[0]];
         const int kind = r0->field == PERMX_FIELD_MODP ? 0
                          : r0->field == PERMX_FIELD_F64 ? (r0->x64 ? 3 : 1) : (r0->x64 ? 4 : 2);
+        const int64_t waves = std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)(longest / chunk_time(r0))));
         int64_t budget = fixed > 0 ? std::max<int64_t>(1, fixed / (int64_t)by_class.size())
-                                   : (int64_t)sm_count() * dispatch_blocks_per_sm(kind, r0->n) * kRyserThreads;
+                                   : (int64_t)sm_count() * dispatch_blocks_per_sm(kind, r0->n) * kRyserThreads * waves;
         const int64_t share = budget / (2 * (int64_t)idx.size());
         for (size_t i : idx) {
             const uint64_t G = 1ull << act[i]->lg;
