@@ -80,12 +80,13 @@ const char* permx_version(void);
  * is bit-for-bit the same whatever else is in the batch.
  * float64 / complex128 arithmetic (permx_set_fp_arith): PERMX_FP_ARITH_INT
  * (default) runs on the integer pipes.  Row i is scaled by a power of two
- * 2^s_i with 2^s_i sum_j |a_ij| < 2^61 and its entries rounded to even
- * integers (each entry moves by at most 2^-60 sum_j |a_ij|), so the walk's row
- * sums of the rounded matrix are exact int64 values; each term multiplies its
- * n row sums with truncated 62-bit integer mantissas (error at most 4n 2^-59
- * (real) or 16n 2^-59 (complex) times sum_i |r_i|^-1 prod_k |r_k| for the
- * rounded row sums r, about (n-1) 2^-58 relative); each chunk adds its terms
+ * 2^s_i with 2^s_i sum_j |a_ij| in [2^62, 2^63) and its entries rounded to even
+ * integers (each entry moves by at most 2^-62 sum_j |a_ij|), so the walk's row
+ * sums R of the rounded, scaled matrix are exact int64 values (|R_i| < 2^62 + n);
+ * each term multiplies its n row sums with truncated 62-bit integer mantissas
+ * (error at most 16n (real) or 64n (complex) times sum_i |R_i|^-1 prod_k |R_k|,
+ * about 2^-58 sum_j |a_ij| / |r_i| relative per factor for the unscaled row
+ * sum r_i); each chunk adds its terms
  * in 128-bit fixed point (error at most 2^-80 of the sum of the term
  * magnitudes) and the chunk totals are summed as double-doubles.  The result
  * is not exact: it is perm(A) to within these per-term errors summed over the

@@ -18,15 +18,20 @@ extern "C" {
 /* (a * b) >> 62, truncated, for |a|, |b| <= 2^62: the kernels' 64x64 product. */
 int64_t permx_x64_mulhi62(int64_t a, int64_t b);
 
+/* (a * b) >> 64, truncated, for |a| <= 2^62 + 2^32, |b| < 2^63 - 2^32: the
+ * walks' chain factor (a mantissa times a staged row sum). */
+int64_t permx_x64_mulhi64(int64_t a, int64_t b);
+
 /* round(a 2^k) to the nearest integer, ties to even, as staging converts a
  * float entry to the integer-mantissa walk's format (finite a, |a 2^k| < 2^62). */
 int64_t permx_x64_scaled_round(double a, int32_t k);
 
-/* Product of n exact integer row sums R[0..n) (|R| < 2^61) as the real walk
+/* Product of n exact integer row sums R[0..n) (|R| < 2^62 + n) as the real walk
  * forms it (four interleaved chains, then combined): value m * 2^e. */
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out);
 
-/* Complex version: rows (Rr[i] + i Ri[i]); value (re + i im) * 2^e. */
+/* Complex version: rows (Rr[i] + i Ri[i]), |Rr[i]| + |Ri[i]| < 2^62 + 64;
+ * value (re + i im) * 2^e. */
 int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t* re_out, int64_t* im_out,
                        int32_t* e_out);
 

@@ -158,7 +158,7 @@ __device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, co
         // permanent is reported as NaN) and the row staged as zeros
         const bool finite = isfinite(S);
         if (!finite) atomicOr(&bad, 1);
-        const int sig = finite && S > 0.0 ? 60 - ilogb(S) : 0;
+        const int sig = finite && S > 0.0 ? 62 - ilogb(S) : 0;
         sig_row[i] = finite ? sig : kNonFinite;
         atomicAdd(&sig_sum, sig);
     }
@@ -177,12 +177,13 @@ __device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, co
         base[((int64_t)j * ld + i) * W + w] = 0;
     }
     __syncthreads();
-    // the Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij) / 2, exact (entries are even)
+    // the Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij) / 2 = A_{i,n-1}/2 - sum_{j<n-1} A_ij/2,
+    // exact (entries are even), summed in halves so no partial sum leaves int64
     for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
         const int i = e / W, w = e - i * W;
-        int64_t sum = 0;
-        for (int j = 0; j < n; ++j) sum += buf[i * nw + j * W + w];
-        base[((int64_t)n * ld + i) * W + w] = buf[i * nw + (n - 1) * W + w] - sum / 2;
+        int64_t half = 0;
+        for (int j = 0; j < n - 1; ++j) half += buf[i * nw + j * W + w] / 2;
+        base[((int64_t)n * ld + i) * W + w] = buf[i * nw + (n - 1) * W + w] / 2 - half;
     }
     if (threadIdx.x == 0) {
         base[(int64_t)(n + 1) * ld * W] = -(int64_t)sig_sum;

@@ -4,16 +4,20 @@
 // B300 executes FP64 at about 1/74 of its FP32 rate, while 32-bit integer
 // multiplies and adds issue at 1/2 to 1/1 of it.  This walk therefore keeps
 // everything in integers:
-//  - row i is scaled by 2^sigma_i (sum_j |a_ij| 2^sigma_i < 2^61) and rounded
-//    to even int64 entries A_ij (each entry moves by at most
-//    2^-60 sum_j |a_ij|), so every Gray-walk row sum
-//    R_i = X_i + sum_{j in S} A_ij of the rounded matrix is exact (no drift);
-//  - a product of row sums is a float with a signed 62-bit mantissa m
-//    (|m| in [2^61, 2^62], complex: the larger component in [2^60, 2^61]) and
-//    an int exponent; each factor is one truncated 64x64 -> 128-bit product
-//    from three signed 32x32 -> 64-bit multiplies, then a leading-zero
-//    normalisation, so a term carries a truncation error of at most
-//    4n 2^-59 (real) or 16n 2^-59 (complex) times sum_i prod_{k != i} |R_k|;
+//  - row i is scaled by 2^sigma_i (sum_j |a_ij| 2^sigma_i < 2^63; complex:
+//    the sum of |Re| + |Im|) and rounded to even int64 entries A_ij (each
+//    entry moves by at most 2^-62 sum_j |a_ij|), so every Gray-walk row sum
+//    R_i = X_i + sum_{j in S} A_ij of the rounded matrix is exact (no drift)
+//    and |R_i| < 2^62 + n (complex: |Re R_i| + |Im R_i| < 2^62 + 2n);
+//  - a product of row sums is a float with a signed mantissa m (|m| in
+//    [2^61, 2^62 + 2^10]; complex: |Re m| + |Im m| <= 2^62 + 2^10) and an int
+//    exponent.  A chain factor is m R >> 64, a combining factor m m' >> 62,
+//    each one truncated 64x64 -> 128-bit product from three signed
+//    32x32 -> 64-bit multiplies, then a leading-zero normalisation (a chain
+//    that is a single row sum enters the combining products as R itself), so
+//    a term carries a truncation error of at most 16n times
+//    sum_i prod_{k != i} |R_k| (complex: 64n), i.e. about 2^-58 relative per
+//    factor;
 //  - each chunk adds its terms into a 128-bit fixed-point accumulator whose
 //    grid follows the chunk's first term (error at most 2^-80 of the sum of
 //    the term magnitudes), and hands the chunk total on as a double-double
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
 #pragma unroll
                 for (int q = 0; q < 4 && q < N; ++q) t[q] = x64_from_int(R[q]);
 #pragma unroll
-                for (int i = 4; i < N; ++i) t[i & 3] = x64_mul(t[i & 3], R[i], 0);
+                for (int i = 4; i < N; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
                 XReal p = t[0];
                 if (N >= 2) p = x64_mul(p, t[1].m, t[1].e);
                 if (N >= 4) {
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
 #pragma unroll
                 for (int q = 0; q < 4 && q < N; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
 #pragma unroll
-                for (int i = 4; i < N; ++i) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+                for (int i = 4; i < N; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
                 XCplx p = t[0];
                 if (N >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
                 if (N >= 4) {
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 for (int q = 0; q < 4; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
 #pragma unroll
                 for (int i = 4; i < H; ++i)
-                    if (i < rows) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+                    if (i < rows) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
                 XCplx p = x64c_mul(t[0], t[1].re, t[1].im, t[1].e);
                 const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
                 p = x64c_mul(p, p23.re, p23.im, p23.e);
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
                 XCplx t = x64c_from_int(Rr[0], Ri[0]);
 #pragma unroll
                 for (int r = 1; r < RQ; ++r)
-                    if (q + 4 * r < N) t = x64c_mul(t, Rr[r], Ri[r], 0);
+                    if (q + 4 * r < N) t = x64c_mul_row(t, Rr[r], Ri[r]);
                 const int q0 = lane & ~3;
                 const XCplx t0 = shfl_cplx(quad, t, q0), t1 = shfl_cplx(quad, t, q0 + 1);
                 const XCplx t2 = shfl_cplx(quad, t, q0 + 2), t3 = shfl_cplx(quad, t, q0 + 3);

@@ -16,13 +16,15 @@ extern "C" {
 
 int64_t permx_x64_mulhi62(int64_t a, int64_t b) { return x64_mulhi62(a, b); }
 
+int64_t permx_x64_mulhi64(int64_t a, int64_t b) { return x64_mulhi64(a, b); }
+
 int64_t permx_x64_scaled_round(double a, int32_t k) { return x64_scaled_round(a, k); }
 
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {
     if (!R || !m_out || !e_out || n < 1 || n > 64) return -1;
     XReal t[4];
     for (int q = 0; q < 4 && q < n; ++q) t[q] = x64_from_int(R[q]);
-    for (int i = 4; i < n; ++i) t[i & 3] = x64_mul(t[i & 3], R[i], 0);
+    for (int i = 4; i < n; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
     XReal p = t[0];
     if (n >= 2) p = x64_mul(p, t[1].m, t[1].e);
     if (n >= 4) {
@@ -41,7 +43,7 @@ int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t*
     if (!Rr || !Ri || !re_out || !im_out || !e_out || n < 1 || n > 64) return -1;
     XCplx t[4];
     for (int q = 0; q < 4 && q < n; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
-    for (int i = 4; i < n; ++i) t[i & 3] = x64c_mul(t[i & 3], Rr[i], Ri[i], 0);
+    for (int i = 4; i < n; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
     XCplx p = t[0];
     if (n >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
     if (n >= 4) {

@@ -27,8 +27,9 @@ __host__ __device__ __forceinline__ int x64_clz(uint64_t v) {
 
 __host__ __device__ __forceinline__ uint32_t x64_hiword(int64_t x) { return (uint32_t)((uint64_t)x >> 32); }
 
-// (a * b) >> 62 for |a|, |b| <= 2^62 (so the result fits), truncated: the
-// result is within [-2, +1] of floor(a*b / 2^62).  Balanced 32-bit limbs
+// (a * b) >> 62 for |a|, |b| <= 2^62 + 2^10 (the result fits; every partial
+// product keeps a margin of 2^31), truncated: the result is within [-2, +1]
+// of floor(a*b / 2^62).  Balanced 32-bit limbs
 // a = a1 2^32 + a0 with a0 in [-2^31, 2^31) keep every partial product a
 // signed 32x32 -> 64 multiply; a0*b0 (< 2^62 in size) is dropped.
 __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
@@ -40,6 +41,21 @@ __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
     const int64_t hh = (int64_t)a1 * (int64_t)b1;
     const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
     return hh * 4 + (mid >> 30);
+}
+
+// (a * b) >> 64 for |a| <= 2^62 + 2^10, |b| < 2^63 - 2^32, truncated (within
+// [-2, +1] of the floor): the same balanced limbs, but the middle products'
+// high word is taken as it is, where the >> 62 form shifts and adds (two
+// fewer ALU operations).  The walks use it for the chain factors, whose row
+// sums are staged two bits larger for it (|R| < 2^62 + n).
+__host__ __device__ __forceinline__ int64_t x64_mulhi64(int64_t a, int64_t b) {
+    const uint32_t al = (uint32_t)(uint64_t)a, bl = (uint32_t)(uint64_t)b;
+    const int32_t a0 = (int32_t)al, b0 = (int32_t)bl;
+    const int32_t a1 = (int32_t)x64_hiword(a) + (int32_t)(al >> 31);
+    const int32_t b1 = (int32_t)x64_hiword(b) + (int32_t)(bl >> 31);
+    const int64_t hh = (int64_t)a1 * (int64_t)b1;
+    const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
+    return hh + (mid >> 32);
 }
 
 // Normalisation works on the high 32-bit word only: |x| is at most 2^62, so
@@ -103,7 +119,8 @@ __host__ __device__ __forceinline__ int64_t x64_scaled_round(double a, int k) {
 struct XReal { int64_t m; int e; };
 struct XCplx { int64_t re, im; int e; };
 
-// real: mantissa target |m| in [2^61, 2^62]
+// real: mantissa target |m| in [2^61, 2^62] (up to 2^62 + 2^10 where a staged
+// row sum or a product of such enters un-normalised: the shift is never negative)
 // Position of the most significant non-sign bit of the high word (-1 when the
 // word is 0 or -1): bfind.s32 on the GPU, the same value from the folded
 // magnitude on the host.
@@ -134,14 +151,21 @@ __host__ __device__ __forceinline__ XReal x64_mul(XReal a, int64_t m2, int e2) {
     const int s = x64_norm_shift_top<62>(x64_top_hi(x));
     return XReal{x64_shl(x, s), a.e + e2 + 62 - s};
 }
+// a times a staged row sum R (|R| < 2^62 + 2^32): the chain factor
+__host__ __device__ __forceinline__ XReal x64_mul_row(XReal a, int64_t R) {
+    const int64_t x = x64_mulhi64(a.m, R);
+    const int s = x64_norm_shift_top<62>(x64_top_hi(x));
+    return XReal{x64_shl(x, s), a.e + 64 - s};
+}
 
-// complex: larger component target in [2^60, 2^61] (sums of two stay below 2^62)
+// complex: larger component target in [2^60, 2^61]; the invariant the products
+// need is |re| + |im| <= 2^62 + 2^10, which every product keeps
 __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) {
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), -s};
 }
-// (a.re + i a.im) * (br + i bi) * 2^-62, |br|, |bi| <= 2^61; three products
+// (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^10; three products
 // (Karatsuba).  A schoolbook form with each operand split into limbs once and
 // all twelve 32x32 -> 64 products chained as multiply-adds measured 4-6 %
 // slower on B300 despite fewer source operations.
@@ -153,6 +177,16 @@ __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t 
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
+}
+// a times a staged complex row sum (|br| + |bi| < 2^62 + 2^32): the chain factor
+__host__ __device__ __forceinline__ XCplx x64c_mul_row(XCplx a, int64_t br, int64_t bi) {
+    const int64_t k1 = x64_mulhi64(a.re + a.im, br);
+    const int64_t k2 = x64_mulhi64(a.re, bi - br);
+    const int64_t k3 = x64_mulhi64(a.im, br + bi);
+    const int64_t re = k1 - k3, im = k1 + k2;
+    const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
+    const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
+    return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + 64 - s};
 }
 
 // Fixed-point sum of one chunk's terms: value = acc * 2^E.  The first

@@ -18,6 +18,8 @@ def lib():
     L = px._lib
     L.permx_x64_mulhi62.argtypes = [ctypes.c_int64, ctypes.c_int64]
     L.permx_x64_mulhi62.restype = ctypes.c_int64
+    L.permx_x64_mulhi64.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    L.permx_x64_mulhi64.restype = ctypes.c_int64
     P = ctypes.POINTER
     L.permx_x64_product.argtypes = [P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int32)]
     L.permx_x64c_product.argtypes = [P(ctypes.c_int64), P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64),
@@ -44,6 +46,23 @@ def test_mulhi62_truncation_bound(lib):
         assert -2 <= got - exact <= 1, (a, b, got, exact)
 
 
+def test_mulhi64_truncation_bound(lib):
+    """The chain factor's product: |a| <= 2^62 + 2^32 (a mantissa, or an
+    un-normalised first row sum), |b| < 2^63 - 2^32 (a row sum, or the Karatsuba
+    sum/difference of two row-sum components)."""
+    rnd = random.Random(2)
+    amax, bmax = 2 ** 62 + 2 ** 32, 2 ** 63 - 2 ** 32 - 1
+    edge_a = [0, 1, -1, amax, -amax, 2 ** 62, -(2 ** 62), 2 ** 61, -(2 ** 61), 2 ** 31, -(2 ** 31), 2 ** 31 - 1]
+    edge_b = [0, 1, -1, bmax, -bmax, 2 ** 62 + 64, -(2 ** 62) - 64, 2 ** 31, -(2 ** 31), 2 ** 32 - 1, 777]
+    cases = [(a, b) for a in edge_a for b in edge_b]
+    cases += [(rnd.randint(-amax, amax), rnd.randint(-bmax, bmax)) for _ in range(20000)]
+    cases += [(rnd.randint(-amax, amax), rnd.randint(-2 ** 40, 2 ** 40)) for _ in range(5000)]
+    for a, b in cases:
+        got = lib.permx_x64_mulhi64(a, b)
+        exact = (a * b) >> 64
+        assert -2 <= got - exact <= 1, (a, b, got, exact)
+
+
 def _error_scale(R):
     """sum_i 2^61 prod_{k != i} max(|R_k|, 2^32): the size one truncation per factor
     can reach.  Normalisation looks at the high 32-bit word only, so a factor below
@@ -63,10 +82,14 @@ def _error_scale(R):
 def test_real_product(lib, n):
     rnd = random.Random(n)
     for trial in range(300):
+        # staged row sums: |R| < 2^62 + n (row scale 2^sigma with sum_j |a_ij| 2^sigma < 2^63)
+        top = 2 ** 62 + n
         if trial % 10 == 0:
-            R = [rnd.randint(-2 ** 61 + 1, 2 ** 61 - 1) >> rnd.randint(0, 40) for _ in range(n)]
+            R = [rnd.randint(-top, top) >> rnd.randint(0, 40) for _ in range(n)]
+        elif trial % 10 == 1:
+            R = [rnd.choice((-top, top)) for _ in range(n)]
         else:
-            R = [rnd.randint(-2 ** 61 + 1, 2 ** 61 - 1) for _ in range(n)]
+            R = [rnd.randint(-top, top) for _ in range(n)]
         if trial == 5:
             R[n // 2] = 0
         a, pa = _arr(R)
@@ -79,18 +102,26 @@ def test_real_product(lib, n):
         assert abs(got - exact) <= Fraction(4 * n, 2 ** 59) * _error_scale(R) + 0, (R, m.value, e.value)
         if exact == 0:
             assert m.value == 0
+        # mantissas: |m| <= 2^62 + 2^10 (a chain that is a lone staged row sum enters the
+        # combining products un-normalised, up to 2^62 + n; the overflow margin is 2^31)
         elif min(abs(r) for r in R) >= 2 ** 40:
-            assert 2 ** 61 <= abs(m.value) <= 2 ** 62
+            assert 2 ** 61 <= abs(m.value) <= 2 ** 62 + 2 ** 10
         else:                      # tiny row sums may leave the mantissa partly normalised
-            assert abs(m.value) <= 2 ** 62
+            assert abs(m.value) <= 2 ** 62 + 2 ** 10
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 11, 26])
 def test_complex_product(lib, n):
     rnd = random.Random(100 + n)
     for trial in range(200):
-        Rr = [rnd.randint(-2 ** 60, 2 ** 60) for _ in range(n)]
-        Ri = [rnd.randint(-2 ** 60, 2 ** 60) for _ in range(n)]
+        # staged complex row sums: |Re R| + |Im R| < 2^62 + 64
+        top = 2 ** 62 + 64
+        Rr, Ri = [], []
+        for _ in range(n):
+            mag = top if trial % 5 == 1 else rnd.randint(0, top)
+            x = rnd.randint(0, mag)
+            Rr.append(x * rnd.choice((-1, 1)))
+            Ri.append((mag - x) * rnd.choice((-1, 1)))
         if trial % 7 == 0:
             Rr[0] >>= 30
             Ri[0] >>= 30
@@ -107,7 +138,7 @@ def test_complex_product(lib, n):
         bound = Fraction(16 * n, 2 ** 59) * _error_scale(mags)
         assert abs(Fraction(re.value) * scale - er) <= bound
         assert abs(Fraction(im.value) * scale - ei) <= bound
-        assert max(abs(re.value), abs(im.value)) <= 2 ** 61
+        assert abs(re.value) + abs(im.value) <= 2 ** 62 + 2 ** 10
 
 
 def test_accumulator_exact_sum(lib):
