@@ -513,6 +513,9 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
     ms, clocks = _clocked(timed)
     t = ms / 1e3
     _close(plans, graph)
+    terms_by_field = {cplx: float(np.sum(v[1].astype(np.float64) * 2.0 ** (v[1] - 1))) for cplx, v in fields.items()}
+    rooflines = _fp_rooflines(px, torch.cuda.get_device_properties(0).multi_processor_count,
+                              terms_by_field.get(True, 0.0), terms_by_field.get(False, 0.0), t)
     # 4) oracle check, one matrix of every (ensemble, n) (the first of its group)
     worst_rel, checked, oracle_terms, oracle_s = 0.0, 0, 0.0, 0.0
     samples = []
@@ -606,7 +609,7 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
             "per_size": per_size, "tuned_chunk_log2": table, "tune_file": tune_path, "tune_s": tune_s,
             "generate_s": gen_s, "oracle_checked": checked, "max_rel_err_vs_oracle": worst_rel,
             "launch": "one CUDA graph (perm_graph_*) of two plans, every (field, n) walk a parallel branch",
-            "clocks": clocks, "dtype": "c128+f64",
+            "clocks": clocks, "dtype": "c128+f64", **rooflines,
             "data": "synthetic, generated on the device (seeded torch generators)",
             "cpu_baseline": {"value": oracle_rate, "unit": "terms/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"perm_dp (double-double row-expansion DP) on the {checked} checked "
@@ -622,6 +625,39 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
                        "complex128": list(CPLX), "float64": list(REAL),
                        "warmup": "one replay of a graph of the same kernels on 1/1000 of the batch",
                        "l2": f"inputs {input_bytes / 2 ** 30:.2f} GiB, read once per step (larger than L2)"}}
+
+
+def _fp_rooflines(px, sms, terms_c, terms_r, t):
+    """Pipe rooflines of the float walks over the batch's evaluated terms
+    (n 2^(n-1) per matrix, split by field), from the library's issue-rate
+    probes run in this process (8 independent chains per thread, 8 blocks of
+    256 threads per SM):
+    - `roofline`: the walk's own arithmetic, one term = the int64 row-sum
+      update(s) and one integer-mantissa chain factor (probe kinds 16 / 17),
+      i.e. the Gray step's work without its bookkeeping, accumulation and
+      dependencies; bound time = terms_c / R_17 + terms_r / R_16;
+    - `fp64_roofline`: the same terms in IEEE float64 on the FP64 pipe
+      (kinds 11 / 10: complex: two adds and a complex multiply; real: an add
+      and a multiply); a fraction above 1 is the integer walk running faster
+      than any FP64 walk could."""
+    rates = {}
+    for name, kind in (("x64_real_term", 16), ("x64_complex_term", 17), ("fp64_real_term", 10),
+                       ("fp64_complex_term", 11)):
+        px.permx_peak_probe(kind, sms * 8, 256, 512)               # warm-up
+        rates[name], _ = px.permx_peak_probe(kind, sms * 8, 256, 4096)
+    terms = terms_c + terms_r
+    t_int = terms_c / rates["x64_complex_term"] + terms_r / rates["x64_real_term"]
+    t_fp64 = terms_c / rates["fp64_complex_term"] + terms_r / rates["fp64_real_term"]
+    return {"roofline": {"bound": "alu", "achieved": terms / t / 1e12, "peak": terms / t_int / 1e12,
+                         "unit": "Tterms/s", "frac": t_int / t, "kernel": "ryser_x64c*/ryser_x64r walks (whole graph)",
+                         "peak_source": "integer-pipe bound of one row-sum update + one chain factor per term, "
+                                        "from permx_peak_probe kinds 16/17 in this process, weighted by the "
+                                        f"batch's terms ({terms_c / terms:.3f} complex)",
+                         "probe_rates_ops_per_s": rates},
+            "fp64_roofline": {"bound": "fp64", "achieved": terms / t / 1e12, "peak": terms / t_fp64 / 1e12,
+                              "unit": "Tterms/s", "frac": t_fp64 / t,
+                              "peak_source": "the same terms in IEEE float64 at the FP64-pipe rate of "
+                                             "permx_peak_probe kinds 10/11"}}
 
 
 def _mix_rate(per_size, count):

@@ -461,6 +461,25 @@ int perm_sample_stats(int field, const void* values, int64_t count, double thres
 int perm_sample_histogram(int field, const void* values, int64_t count, int kind, const double* edges,
                           int32_t nedges, int64_t* counts, void* stream);
 
+/* Measurement hook (the paper has no counterpart): issue-rate probe of one
+ * operation kind, the denominator of the walks' pipe rooflines.  Runs
+ * `blocks` x `threads` threads (threads in [32, 1024]), each with 8
+ * independent chains of `iters` operations, on the current device and
+ * stream 0 (synchronous); *ops_per_s = blocks*threads*iters*8 / time,
+ * *ms_out (may be NULL) = the CUDA-event time of the timed launch.  Kinds:
+ *   0 fma.rn.f64   1 add.rn.f64   2 mul.rn.f64   3 fma.rn.f32
+ *   4 mad.lo.u32   5 mul.wide.u32 6 mul.hi.u32   7 add.u32   8 min.u32
+ *   9 one F_p term (modular add + Montgomery product)
+ *  10 one float64 term in FP64 (add + multiply)
+ *  11 one complex128 term in FP64 (2 adds + complex multiply)
+ *  12 clz.b64   13 clz.b32
+ *  14 one real integer-mantissa combining factor (m m' >> 62)
+ *  15 one complex integer-mantissa combining factor
+ *  16 one real integer-mantissa term (int64 row-sum update + chain factor m R >> 64)
+ *  17 one complex integer-mantissa term (two int64 updates + complex chain factor)
+ * Errors: EINVAL (bad kind or sizes, NULL ops_per_s), ENOMEM, ECUDA. */
+int permx_peak_probe(int kind, int blocks, int threads, int iters, double* ops_per_s, double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

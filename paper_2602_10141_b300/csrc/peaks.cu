@@ -11,6 +11,8 @@
 //  10 one float64 unit (add + multiply)  11 one complex128 unit (2 adds + complex multiply)
 //  12 clz.b64   13 clz.b32   14 one real integer-mantissa factor (x64_mul)
 //  15 one complex integer-mantissa factor (x64c_mul)
+//  16 one real integer-mantissa term: int64 row-sum update + chain factor (x64_mul_row)
+//  17 one complex integer-mantissa term: two int64 updates + chain factor (x64c_mul_row)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +30,17 @@ __global__ void peak_kernel(int iters, uint32_t seed, unsigned long long* sink) 
     uint32_t t[8];
     double2 c[8], cr[8];
     const uint32_t p = 2147483629u, pinv = 1681680005u;   // any odd p and its inverse mod 2^32
+    // kinds 16 / 17: staged-size row sums (|Re| + |Im| < 2^62) and normalised mantissas
+    int64_t Rr[8], Ri[8];
+    XReal xr[8];
+    XCplx xc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        Rr[k] = 0x2d00000000000000ll + ((int64_t)(tid + k) << 20);
+        Ri[k] = 0x1200000000000000ll - ((int64_t)(3 * tid + k) << 18);
+        xr[k] = XReal{0x3000000000000000ll + k, 0};
+        xc[k] = XCplx{0x1800000000000000ll + k, 0x0c00000000000000ll - k, 0};
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         d[k] = 1.0 + k * 1e-3 + tid * 1e-9;
@@ -38,8 +51,18 @@ __global__ void peak_kernel(int iters, uint32_t seed, unsigned long long* sink) 
         cr[k] = make_double2(0.75, -0.5 + k * 1e-3);
     }
     for (int it = 0; it < iters; ++it) {
+        const int64_t dv = (it & 1) ? (int64_t)v << 24 : -((int64_t)v << 24);   // row sums stay in range
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
+            if (KIND == 16) {
+                Rr[k] += dv;
+                xr[k] = x64_mul_row(xr[k], Rr[k]);
+            }
+            if (KIND == 17) {
+                Rr[k] += dv;
+                Ri[k] -= dv;
+                xc[k] = x64c_mul_row(xc[k], Rr[k], Ri[k]);
+            }
             if (KIND == 0) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d[k]) : "d"(e), "d"(f));
             if (KIND == 1) asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(d[k]) : "d"(f));
             if (KIND == 2) asm volatile("mul.rn.f64 %0, %0, %1;" : "+d"(d[k]) : "d"(e));
@@ -93,7 +116,8 @@ __global__ void peak_kernel(int iters, uint32_t seed, unsigned long long* sink) 
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         acc += (unsigned long long)(d[k] * 1e6) + (unsigned long long)(fl[k] * 1e3f) + u[k] + t[k] +
-               (unsigned long long)(c[k].x * 1e6);
+               (unsigned long long)(c[k].x * 1e6) + (unsigned long long)(xr[k].m ^ xr[k].e) +
+               (unsigned long long)(xc[k].re ^ xc[k].im ^ xc[k].e);
     if (acc == 0x123456789ull) *sink = acc;   // practically never; keeps the chains live
 }
 
@@ -120,6 +144,7 @@ using namespace permx;
 
 extern "C" int permx_peak_probe(int kind, int blocks, int threads, int iters, double* ops_per_s, double* ms_out) {
     if (!ops_per_s || blocks < 1 || threads < 32 || threads > 1024 || iters < 1) return fail(PERMX_EINVAL, "bad arguments");
+    if (kind < 0 || kind > 17) return fail(PERMX_EINVAL, "bad probe kind");
     unsigned long long* sink = nullptr;
     PERMX_CUDA(cudaMalloc(&sink, sizeof(unsigned long long)));
     float ms = 0.f;
@@ -141,6 +166,8 @@ extern "C" int permx_peak_probe(int kind, int blocks, int threads, int iters, do
         case 13: e = run_probe<13>(blocks, threads, iters, sink, &ms); break;
         case 14: e = run_probe<14>(blocks, threads, iters, sink, &ms); break;
         case 15: e = run_probe<15>(blocks, threads, iters, sink, &ms); break;
+        case 16: e = run_probe<16>(blocks, threads, iters, sink, &ms); break;
+        case 17: e = run_probe<17>(blocks, threads, iters, sink, &ms); break;
         default: break;
     }
     cudaFree(sink);

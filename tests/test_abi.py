@@ -92,6 +92,11 @@ def test_invalid_helper_arguments(px):
         px.perm_crt([1, 2], [7, 7])
     with pytest.raises(px.PermxError):
         px.perm_schur_residues(0, 7, 2)
+    # the issue-rate probe checks its kind and sizes before any CUDA call
+    for args in ((18, 1, 256, 1), (-1, 1, 256, 1), (0, 0, 256, 1), (0, 1, 16, 1), (0, 1, 256, 0)):
+        with pytest.raises(px.PermxError) as e:
+            px.permx_peak_probe(*args)
+        assert e.value.code == px.PERMX_EINVAL
 
 
 def test_chunk_tuning_table_host_logic(px):
