@@ -22,6 +22,24 @@ int64_t permx_x64_mulhi62(int64_t a, int64_t b);
  * walks' chain factor (a mantissa times a staged row sum). */
 int64_t permx_x64_mulhi64(int64_t a, int64_t b);
 
+/* Both products above as the GPU computes them, for count (1..2^20) pairs of
+ * HOST arrays a, b; results to HOST arrays hi62, hi64.  Synchronous, on the
+ * current device; the caller checks them against the host forms.  Errors:
+ * PERMX_EINVAL (NULL pointer, count out of range), PERMX_ENOMEM, PERMX_ECUDA. */
+int permx_x64_mulhi_device(const int64_t* a, const int64_t* b, int64_t count, int64_t* hi62, int64_t* hi64);
+
+/* Complex product (ar + i ai)(br + i bi) >> sh by components (sh = 64: the
+ * walks' chain factor; sh = 62: the combining factor), for
+ * |ar| + |ai|, |br| + |bi| <= 2^62 + 2^10: Karatsuba on the truncated products
+ * above, each component within 4 of the exact value.  Returns PERMX_EINVAL for
+ * another sh or a NULL output. */
+int permx_x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int32_t sh, int64_t* re, int64_t* im);
+
+/* The same on the GPU for count (1..2^20) HOST 4-tuples in4 = (ar, ai, br, bi):
+ * out4 (HOST) = (re, im) for sh = 64, then (re, im) for sh = 62.  Synchronous.
+ * Errors: PERMX_EINVAL, PERMX_ENOMEM, PERMX_ECUDA. */
+int permx_x64c_mulhi_device(const int64_t* in4, int64_t count, int64_t* out4);
+
 /* round(a 2^k) to the nearest integer, ties to even, as staging converts a
  * float entry to the integer-mantissa walk's format (finite a, |a 2^k| < 2^62). */
 int64_t permx_x64_scaled_round(double a, int32_t k);

@@ -36,7 +36,7 @@ INSTANCES = {
     "inst_x64r.cu": [(1, 11), (12, 22), (23, 32)],
     "inst_x64c.cu": [(1, 8), (9, 16), (17, 24), (25, 32)],
 }
-PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu", "noalloc.cu", "plan.cu", "stats.cu", "gather.cu"]
+PLAIN_CU = ["batch.cu", "dispatch.cu", "peaks.cu", "noalloc.cu", "plan.cu", "stats.cu", "gather.cu", "selftest_dev.cu"]
 PLAIN_CPP = ["api.cpp", "field.cpp", "schur.cpp", "serve.cpp", "selftest.cpp"]
 
 

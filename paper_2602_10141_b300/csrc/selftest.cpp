@@ -18,6 +18,13 @@ int64_t permx_x64_mulhi62(int64_t a, int64_t b) { return x64_mulhi62(a, b); }
 
 int64_t permx_x64_mulhi64(int64_t a, int64_t b) { return x64_mulhi64(a, b); }
 
+int permx_x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int32_t sh, int64_t* re, int64_t* im) {
+    if (!re || !im || (sh != 62 && sh != 64)) return PERMX_EINVAL;
+    if (sh == 64) x64c_mulhi<64>(ar, ai, br, bi, *re, *im);
+    else x64c_mulhi<62>(ar, ai, br, bi, *re, *im);
+    return PERMX_OK;
+}
+
 int64_t permx_x64_scaled_round(double a, int32_t k) { return x64_scaled_round(a, k); }
 
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {

@@ -27,35 +27,81 @@ __host__ __device__ __forceinline__ int x64_clz(uint64_t v) {
 
 __host__ __device__ __forceinline__ uint32_t x64_hiword(int64_t x) { return (uint32_t)((uint64_t)x >> 32); }
 
+// Signed 32x32 -> 64-bit multiply-add, a b + c: one mad.wide.s32 on the GPU
+// (the addition rides on the integer-multiply pipe); the host computes the
+// same exact integer.
+__host__ __device__ __forceinline__ int64_t x64_madw(int32_t a, int32_t b, int64_t c) {
+#ifdef __CUDA_ARCH__
+    long long r;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"((long long)c));
+    return r;
+#else
+    return (int64_t)a * (int64_t)b + c;
+#endif
+}
+
+// Signed 32x32 -> 64-bit product (mul.wide.s32): the first term of a chain of
+// multiply-adds, so that no zero addend has to be held in registers.
+__host__ __device__ __forceinline__ int64_t x64_mulw(int32_t a, int32_t b) {
+#ifdef __CUDA_ARCH__
+    long long r;
+    asm("mul.wide.s32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(b));
+    return r;
+#else
+    return (int64_t)a * (int64_t)b;
+#endif
+}
+
+// Balanced 32-bit limbs a = hi 2^32 + lo with lo in [-2^31, 2^31): every
+// partial product is then a signed 32x32 -> 64 multiply.  hi is the high word
+// plus the low word's top bit.
+struct XLimbs {
+    int32_t hi, lo;
+};
+__host__ __device__ __forceinline__ XLimbs x64_limbs(int64_t a) {
+    const uint32_t al = (uint32_t)(uint64_t)a;
+    return XLimbs{(int32_t)x64_hiword(a) + (int32_t)(al >> 31), (int32_t)al};
+}
+
 // (a * b) >> 62 for |a|, |b| <= 2^62 + 2^10 (the result fits; every partial
 // product keeps a margin of 2^31), truncated: the result is within [-2, +1]
-// of floor(a*b / 2^62).  Balanced 32-bit limbs
-// a = a1 2^32 + a0 with a0 in [-2^31, 2^31) keep every partial product a
-// signed 32x32 -> 64 multiply; a0*b0 (< 2^62 in size) is dropped.
+// of floor(a*b / 2^62).  The low product a0*b0 (< 2^62 in size) is dropped;
+// the rest is 4 (a1 b1 + floor(mid / 2^32)) + bits 30..31 of mid, with
+// mid = a1 b0 + a0 b1, all in multiply-adds.
 __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
-    const uint32_t al = (uint32_t)(uint64_t)a, bl = (uint32_t)(uint64_t)b;
-    const int32_t a0 = (int32_t)al, b0 = (int32_t)bl;
-    // a = a1 2^32 + a0 with a0 = al - 2^32 when al >= 2^31: a1 = high word + that carry
-    const int32_t a1 = (int32_t)x64_hiword(a) + (int32_t)(al >> 31);
-    const int32_t b1 = (int32_t)x64_hiword(b) + (int32_t)(bl >> 31);
-    const int64_t hh = (int64_t)a1 * (int64_t)b1;
-    const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
-    return hh * 4 + (mid >> 30);
+    const XLimbs x = x64_limbs(a), y = x64_limbs(b);
+    const int64_t mid = x64_madw(x.lo, y.hi, x64_mulw(x.hi, y.lo));
+    const int64_t r = x64_madw(x.hi, y.hi, mid >> 32);
+    return (int64_t)(((uint64_t)r << 2) | (((uint64_t)mid >> 30) & 3u));
 }
 
 // (a * b) >> 64 for |a| <= 2^62 + 2^10, |b| < 2^63 - 2^32, truncated (within
-// [-2, +1] of the floor): the same balanced limbs, but the middle products'
-// high word is taken as it is, where the >> 62 form shifts and adds (two
-// fewer ALU operations).  The walks use it for the chain factors, whose row
-// sums are staged two bits larger for it (|R| < 2^62 + n).
+// [-2, +1] of the floor): a1 b1 + floor(mid / 2^32).  The walks use it for the
+// chain factors, whose row sums are staged two bits larger for it
+// (|R| < 2^62 + n).
 __host__ __device__ __forceinline__ int64_t x64_mulhi64(int64_t a, int64_t b) {
-    const uint32_t al = (uint32_t)(uint64_t)a, bl = (uint32_t)(uint64_t)b;
-    const int32_t a0 = (int32_t)al, b0 = (int32_t)bl;
-    const int32_t a1 = (int32_t)x64_hiword(a) + (int32_t)(al >> 31);
-    const int32_t b1 = (int32_t)x64_hiword(b) + (int32_t)(bl >> 31);
-    const int64_t hh = (int64_t)a1 * (int64_t)b1;
-    const int64_t mid = (int64_t)a1 * (int64_t)b0 + (int64_t)a0 * (int64_t)b1;
-    return hh + (mid >> 32);
+    const XLimbs x = x64_limbs(a), y = x64_limbs(b);
+    const int64_t mid = x64_madw(x.lo, y.hi, x64_mulw(x.hi, y.lo));
+    return x64_madw(x.hi, y.hi, mid >> 32);
+}
+
+// Complex product (ar + i ai)(br + i bi) >> SH by components (SH = 64: chain
+// factor, b a staged row sum; SH = 62: combining factor, b a mantissa), for
+// |ar| + |ai| <= 2^62 + 2^10 and |br| + |bi| <= 2^62 + 2^10: three products
+// (Karatsuba), re = k1 - k3, im = k1 + k2, each k within [-2, +1] of its
+// floor, so each component is within 4 of the exact (ar br - ai bi) 2^-SH
+// (resp. (ar bi + ai br) 2^-SH).  A schoolbook form on twelve chained
+// multiply-adds (the subtraction as a product with -ai) issues fewer
+// instructions (64.8 against 67.4 per complex term at n = 20) but its longer
+// dependency chains made it 2 % slower at n = 23 on B300.
+template <int SH>
+__host__ __device__ __forceinline__ void x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int64_t& re,
+                                                    int64_t& im) {
+    const int64_t k1 = SH == 64 ? x64_mulhi64(ar + ai, br) : x64_mulhi62(ar + ai, br);
+    const int64_t k2 = SH == 64 ? x64_mulhi64(ar, bi - br) : x64_mulhi62(ar, bi - br);
+    const int64_t k3 = SH == 64 ? x64_mulhi64(ai, br + bi) : x64_mulhi62(ai, br + bi);
+    re = k1 - k3;
+    im = k1 + k2;
 }
 
 // Normalisation works on the high 32-bit word only: |x| is at most 2^62, so
@@ -165,25 +211,18 @@ __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) 
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), -s};
 }
-// (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^10; three products
-// (Karatsuba).  A schoolbook form with each operand split into limbs once and
-// all twelve 32x32 -> 64 products chained as multiply-adds measured 4-6 %
-// slower on B300 despite fewer source operations.
+// (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^10: the combining factor
 __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t bi, int eb) {
-    const int64_t k1 = x64_mulhi62(a.re + a.im, br);
-    const int64_t k2 = x64_mulhi62(a.re, bi - br);
-    const int64_t k3 = x64_mulhi62(a.im, br + bi);
-    const int64_t re = k1 - k3, im = k1 + k2;
+    int64_t re, im;
+    x64c_mulhi<62>(a.re, a.im, br, bi, re, im);
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
 }
-// a times a staged complex row sum (|br| + |bi| < 2^62 + 2^32): the chain factor
+// a times a staged complex row sum (|br| + |bi| < 2^62 + 2n): the chain factor
 __host__ __device__ __forceinline__ XCplx x64c_mul_row(XCplx a, int64_t br, int64_t bi) {
-    const int64_t k1 = x64_mulhi64(a.re + a.im, br);
-    const int64_t k2 = x64_mulhi64(a.re, bi - br);
-    const int64_t k3 = x64_mulhi64(a.im, br + bi);
-    const int64_t re = k1 - k3, im = k1 + k2;
+    int64_t re, im;
+    x64c_mulhi<64>(a.re, a.im, br, bi, re, im);
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + 64 - s};

@@ -20,6 +20,8 @@ def lib():
     L.permx_x64_mulhi62.restype = ctypes.c_int64
     L.permx_x64_mulhi64.argtypes = [ctypes.c_int64, ctypes.c_int64]
     L.permx_x64_mulhi64.restype = ctypes.c_int64
+    L.permx_x64c_mulhi.argtypes = [ctypes.c_int64] * 4 + [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                                          ctypes.POINTER(ctypes.c_int64)]
     P = ctypes.POINTER
     L.permx_x64_product.argtypes = [P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64), P(ctypes.c_int32)]
     L.permx_x64c_product.argtypes = [P(ctypes.c_int64), P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64),
@@ -61,6 +63,32 @@ def test_mulhi64_truncation_bound(lib):
         got = lib.permx_x64_mulhi64(a, b)
         exact = (a * b) >> 64
         assert -2 <= got - exact <= 1, (a, b, got, exact)
+
+
+def _cplx_operand(rnd, top):
+    """A complex operand with |re| + |im| <= top, its size drawn from the full range."""
+    mag = rnd.choice((top, rnd.randint(0, top), rnd.randint(0, top) >> rnd.randint(0, 60)))
+    x = rnd.randint(0, mag)
+    return x * rnd.choice((-1, 1)), (mag - x) * rnd.choice((-1, 1))
+
+
+def test_complex_mulhi_components_bound(lib):
+    """(ar + i ai)(br + i bi) >> 64 (chain factor) and >> 62 (combining factor):
+    each component within 4 of the exact value's floor (Karatsuba: three
+    truncated products, each within [-2, +1] of its floor)."""
+    rnd = random.Random(3)
+    top = 2 ** 62 + 2 ** 10
+    re, im = ctypes.c_int64(), ctypes.c_int64()
+    edges = [(top, 0), (-top, 0), (0, top), (0, -top), (top // 2, -(top - top // 2)), (2 ** 31, -(2 ** 31)), (0, 0)]
+    cases = [(a, b) for a in edges for b in edges]
+    cases += [(_cplx_operand(rnd, top), _cplx_operand(rnd, top)) for _ in range(20000)]
+    for (ar, ai), (br, bi) in cases:
+        er, ei = ar * br - ai * bi, ar * bi + ai * br
+        assert lib.permx_x64c_mulhi(ar, ai, br, bi, 64, ctypes.byref(re), ctypes.byref(im)) == 0
+        assert -4 <= re.value - (er >> 64) <= 4 and -4 <= im.value - (ei >> 64) <= 4, (ar, ai, br, bi)
+        assert lib.permx_x64c_mulhi(ar, ai, br, bi, 62, ctypes.byref(re), ctypes.byref(im)) == 0
+        assert -4 <= re.value - (er >> 62) <= 4 and -4 <= im.value - (ei >> 62) <= 4, (ar, ai, br, bi)
+    assert lib.permx_x64c_mulhi(1, 2, 3, 4, 63, ctypes.byref(re), ctypes.byref(im)) != 0
 
 
 def _error_scale(R):
