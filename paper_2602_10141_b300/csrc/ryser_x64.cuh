@@ -128,14 +128,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
                 for (int q = 0; q < 4 && q < N; ++q) t[q] = x64_from_int(R[q]);
 #pragma unroll
                 for (int i = 4; i < N; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
-                XReal p = t[0];
-                if (N >= 2) p = x64_mul(p, t[1].m, t[1].e);
-                if (N >= 4) {
-                    const XReal p23 = x64_mul(t[2], t[3].m, t[3].e);
-                    p = x64_mul(p, p23.m, p23.e);
-                } else if (N == 3) {
-                    p = x64_mul(p, t[2].m, t[2].e);
-                }
+                const XReal p = x64_term(t, N);
                 x64_acc_add(acc, p.m, p.e, k & 1);
             }
         }
@@ -216,14 +209,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
                 for (int q = 0; q < 4 && q < N; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
 #pragma unroll
                 for (int i = 4; i < N; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
-                XCplx p = t[0];
-                if (N >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
-                if (N >= 4) {
-                    const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
-                    p = x64c_mul(p, p23.re, p23.im, p23.e);
-                } else if (N == 3) {
-                    p = x64c_mul(p, t[2].re, t[2].im, t[2].e);
-                }
+                const XCplx p = x64c_term(t, N);
                 x64_acc_add(ar, p.re, p.e, k & 1);
                 x64_acc_add(ai, p.im, p.e, k & 1);
             }
@@ -491,9 +477,8 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
                 const int q0 = lane & ~3;
                 const XCplx t0 = shfl_cplx(quad, t, q0), t1 = shfl_cplx(quad, t, q0 + 1);
                 const XCplx t2 = shfl_cplx(quad, t, q0 + 2), t3 = shfl_cplx(quad, t, q0 + 3);
-                XCplx pr = x64c_mul(t0, t1.re, t1.im, t1.e);
-                const XCplx p23 = x64c_mul(t2, t3.re, t3.im, t3.e);
-                pr = x64c_mul(pr, p23.re, p23.im, p23.e);
+                const XCplx tq[4] = {t0, t1, t2, t3};   // the one-lane walk's four chains
+                const XCplx pr = x64c_term(tq, N);
                 x64_acc_add(ar, pr.re, pr.e, k & 1);
                 x64_acc_add(ai, pr.im, pr.e, k & 1);
             }

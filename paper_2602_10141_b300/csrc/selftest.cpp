@@ -32,14 +32,7 @@ int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_ou
     XReal t[4];
     for (int q = 0; q < 4 && q < n; ++q) t[q] = x64_from_int(R[q]);
     for (int i = 4; i < n; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
-    XReal p = t[0];
-    if (n >= 2) p = x64_mul(p, t[1].m, t[1].e);
-    if (n >= 4) {
-        const XReal p23 = x64_mul(t[2], t[3].m, t[3].e);
-        p = x64_mul(p, p23.m, p23.e);
-    } else if (n == 3) {
-        p = x64_mul(p, t[2].m, t[2].e);
-    }
+    const XReal p = x64_term(t, n);
     *m_out = p.m;
     *e_out = p.e;
     return 0;
@@ -51,14 +44,7 @@ int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t*
     XCplx t[4];
     for (int q = 0; q < 4 && q < n; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
     for (int i = 4; i < n; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
-    XCplx p = t[0];
-    if (n >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
-    if (n >= 4) {
-        const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
-        p = x64c_mul(p, p23.re, p23.im, p23.e);
-    } else if (n == 3) {
-        p = x64c_mul(p, t[2].re, t[2].im, t[2].e);
-    }
+    const XCplx p = x64c_term(t, n);
     *re_out = p.re;
     *im_out = p.im;
     *e_out = p.e;

@@ -228,6 +228,33 @@ __host__ __device__ __forceinline__ XCplx x64c_mul_row(XCplx a, int64_t br, int6
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + 64 - s};
 }
 
+// A term from its four product chains t[0..min(n, 4)) (chain q holds rows
+// q, q + 4, ...): (t0 t1)(t2 t3), or the shorter forms for n < 4.  Leaving
+// the last factor un-normalised (the accumulator takes any mantissa below
+// 2^63) measured within +-2 % either way on B300 and is not done.
+__host__ __device__ __forceinline__ XReal x64_term(const XReal (&t)[4], int n) {
+    XReal p = t[0];
+    if (n >= 2) p = x64_mul(p, t[1].m, t[1].e);
+    if (n >= 4) {
+        const XReal p23 = x64_mul(t[2], t[3].m, t[3].e);
+        p = x64_mul(p, p23.m, p23.e);
+    } else if (n == 3) {
+        p = x64_mul(p, t[2].m, t[2].e);
+    }
+    return p;
+}
+__host__ __device__ __forceinline__ XCplx x64c_term(const XCplx (&t)[4], int n) {
+    XCplx p = t[0];
+    if (n >= 2) p = x64c_mul(p, t[1].re, t[1].im, t[1].e);
+    if (n >= 4) {
+        const XCplx p23 = x64c_mul(t[2], t[3].re, t[3].im, t[3].e);
+        p = x64c_mul(p, p23.re, p23.im, p23.e);
+    } else if (n == 3) {
+        p = x64c_mul(p, t[2].re, t[2].im, t[2].e);
+    }
+    return p;
+}
+
 // Fixed-point sum of one chunk's terms: value = acc * 2^E.  The first
 // term fixes E 24 bits below its mantissa's lowest bit range; a term more
 // than 2^40 above the accumulator scale rescales it first, so at most 2^12
@@ -264,9 +291,9 @@ __host__ __device__ __forceinline__ void x64_acc_add(XAcc& a, int64_t m, int e, 
 // a <- a + b, both aligned to the larger exponent (the smaller-exponent one
 // is shifted right).  The operation is symmetric in a and b, so a fixed
 // butterfly of merges gives the same bits on every lane and in every batch.
-// A term is below 2^102 on its accumulator's grid (mantissa < 2^62, shift
-// <= 40), a chunk of at most 2^16 terms below 2^118, and 32 merges keep the
-// sum below 2^123.
+// A term is below 2^103 on its accumulator's grid (|mantissa| <= 2^62 + 2^10,
+// shift <= 40), a chunk of at most 2^16 terms below 2^119, and 32 merges keep
+// the sum below 2^124.
 __host__ __device__ __forceinline__ __int128 x64_sar128(__int128 v, int d) {
     return d <= 0 ? v : (d < 127 ? (v >> d) : (v < 0 ? (__int128)-1 : (__int128)0));
 }
