@@ -115,6 +115,7 @@ struct ModpLaunch {
     int nfin = 0;
     unsigned* done = nullptr;      // ticket counter, 0 before the launch, reset to 0 by the last block
     uint32_t* out = nullptr;
+    uint32_t zero = 0;             // always 0: keeps the F_p walk's adds on the ALU pipe (ryser_modp.cuh)
 };
 
 struct FpLaunch {

@@ -24,12 +24,21 @@
 
 namespace permx {
 
-__device__ __forceinline__ uint32_t mod_add(uint32_t r, uint32_t a, uint32_t p) {
-    uint32_t s = r + a;           // < 2p < 2^32
+// Pipe placement.  The products need one mul.wide, one mul.lo and one mul.hi
+// each, all on the integer-multiply (fmaheavy) pipe, and that pipe bounds the
+// walk.  ptxas is free to issue a two-operand integer add as a multiply-add
+// on the same pipe, and does so for a share of the Montgomery subtractions
+// and row-sum adds.  The walk therefore adds z, a launch parameter that is
+// always 0 and unknown to the compiler, to each of them: a three-operand add
+// has only the ALU form (IADD3), which leaves the multiply pipe to the
+// multiplies (S_33 walk: 131 -> 100 multiply-pipe instructions per Gray step;
+// the benchmark's five-prime step 259.4 -> 251.1 ms).
+__device__ __forceinline__ uint32_t mod_add(uint32_t r, uint32_t a, uint32_t p, uint32_t z = 0) {
+    uint32_t s = r + a + z;       // < 2p < 2^32
     return min(s, s - p);         // s - p wraps to > p when s < p
 }
-__device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p) {
-    uint32_t d = r - a;           // wraps to > 2^31 > p when r < a
+__device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p, uint32_t z = 0) {
+    uint32_t d = r - a + z;       // wraps to > 2^31 > p when r < a
     return min(d, d + p);
 }
 #ifndef PERMX_MODP_SIGNED
@@ -40,19 +49,19 @@ __device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p) 
 typedef int32_t mont_t;       // product-tree values in (-p, p)
 typedef long long term_acc_t;
 // a * b * 2^-32 mod p for |a|, |b| < p, result in (-p, p)
-__device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, uint32_t p, uint32_t pinv) {
+__device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, uint32_t p, uint32_t pinv, int32_t z) {
     const long long T = (long long)a * b;
     const int32_t m = (int32_t)((uint32_t)(unsigned long long)T * pinv);
     const int32_t mh = __mulhi(m, (int32_t)p);
-    return (int32_t)(T >> 32) - mh;
+    return (int32_t)(T >> 32) - mh + z;
 }
 #else
 typedef uint32_t mont_t;      // product-tree values in [0, p)
 typedef unsigned long long term_acc_t;
 // (-p, p) -> [0, p): a negative value wraps above p, so the unsigned min picks r + p
 __device__ __forceinline__ uint32_t mont_fix(uint32_t r, uint32_t p) { return min(r, r + p); }
-__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
-    uint64_t T = (uint64_t)a * b;
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv, int32_t z) {
+    uint64_t T = (uint64_t)a * b + (uint32_t)z;
     uint32_t m = (uint32_t)T * pinv;
     uint32_t mh = __umulhi(m, p);
     uint32_t r = (uint32_t)(T >> 32) - mh;   // true value in (-p, p)
@@ -65,7 +74,7 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p,
 // level loop has a fixed trip count so that, fully unrolled, every index is a
 // compile-time constant and v[] stays in registers.
 template <int N>
-__device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, uint32_t pinv) {
+__device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, uint32_t pinv, int32_t z) {
     static_assert(N <= 64, "tree depth");
     mont_t v[N];
 #pragma unroll
@@ -76,7 +85,7 @@ __device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, 
         if (w > 1) {
 #pragma unroll
             for (int i = 0; i < N / 2; ++i)
-                if (i < w / 2) v[i] = mont_mul(v[2 * i], v[2 * i + 1], p, pinv);
+                if (i < w / 2) v[i] = mont_mul(v[2 * i], v[2 * i + 1], p, pinv, z);
             if (w & 1) v[w / 2] = v[w - 1];
         }
     }
@@ -86,7 +95,7 @@ __device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, 
 // dst_i = src_i +- (column j)_i mod p
 template <int N, bool SUB>
 __device__ __forceinline__ void column_step(uint32_t (&dst)[N], const uint32_t (&src)[N],
-                                            const uint32_t* __restrict__ cj, uint32_t p) {
+                                            const uint32_t* __restrict__ cj, uint32_t p, uint32_t z) {
     constexpr int NP = pad4(N);
     const uint4* c4 = reinterpret_cast<const uint4*>(cj);
 #pragma unroll
@@ -96,7 +105,7 @@ __device__ __forceinline__ void column_step(uint32_t (&dst)[N], const uint32_t (
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             if (4 * q + e < N)
-                dst[4 * q + e] = SUB ? mod_sub(src[4 * q + e], a[e], p) : mod_add(src[4 * q + e], a[e], p);
+                dst[4 * q + e] = SUB ? mod_sub(src[4 * q + e], a[e], p, z) : mod_add(src[4 * q + e], a[e], p, z);
         }
     }
 }
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
+    const uint32_t z0 = L.zero;   // 0, opaque to the compiler (pipe placement, above)
     // lanes holding chunks of the same matrix form aligned groups of G lanes
     const int G = L.log2_chunks >= 5 ? 32 : (1 << L.log2_chunks);
     // warp-aligned loop: every lane of a warp runs the same number of iterations
@@ -188,7 +198,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             term_acc_t E = 0, O = 0;
             uint64_t k = ks;
             if (k & 1) {                       // a window may start on an odd index
-                O += prod_tree<N>(r, p, pinv);
+                O += prod_tree<N>(r, p, pinv, (int32_t)z0);
                 ++k;
                 if (k < ke) toggle_column<N>(r, col, k, p);
             }
@@ -198,18 +208,18 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             // computed from r and the next r from r2, so no array is copied.
             while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke) {
                 uint32_t r2[N];
-                if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p);
-                else column_step<N, false>(r2, r, col, p);
-                E += prod_tree<N>(r, p, pinv);
-                O += prod_tree<N>(r2, p, pinv);
+                if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
+                else column_step<N, false>(r2, r, col, p, z0);
+                E += prod_tree<N>(r, p, pinv, (int32_t)z0);
+                O += prod_tree<N>(r2, p, pinv, (int32_t)z0);
                 k += 2;
                 if (k >= ke) break;          // the chunk is done; r is not needed again
                 const int j = __ffsll((long long)k) - 1;
-                if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p);
-                else column_step<N, false>(r, r2, col + j * NP, p);
+                if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p, z0);
+                else column_step<N, false>(r, r2, col + j * NP, p, z0);
             }
             for (; k < ke; ++k) {              // remaining steps one at a time
-                if (k & 1) O += prod_tree<N>(r, p, pinv); else E += prod_tree<N>(r, p, pinv);
+                if (k & 1) O += prod_tree<N>(r, p, pinv, (int32_t)z0); else E += prod_tree<N>(r, p, pinv, (int32_t)z0);
                 if (k + 1 < ke) toggle_column<N>(r, col, k + 1, p);
             }
 #if PERMX_MODP_SIGNED
