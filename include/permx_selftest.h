@@ -40,6 +40,12 @@ int permx_x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int32_t sh,
  * Errors: PERMX_EINVAL, PERMX_ENOMEM, PERMX_ECUDA. */
 int permx_x64c_mulhi_device(const int64_t* in4, int64_t count, int64_t* out4);
 
+/* The double nearest to (hi 2^64 + lo) 2^e, ties to even (hi:lo a signed
+ * 128-bit integer), computed in integer operations as the integer-mode
+ * finalisation rounds a matrix's exact fixed-point sum once; subnormal results
+ * are rounded at their own precision, too large ones give +-inf. */
+double permx_x64_to_double(int64_t hi, uint64_t lo, int32_t e);
+
 /* round(a 2^k) to the nearest integer, ties to even, as staging converts a
  * float entry to the integer-mantissa walk's format (finite a, |a 2^k| < 2^62). */
 int64_t permx_x64_scaled_round(double a, int32_t k);

@@ -305,6 +305,13 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_fp_kernel(const double
     __shared__ double sh[4][kFinalThreads];
     finalize_fp_block(partial, f[blockIdx.x], cplx, out, sh);
 }
+// Integer mode: the XPart slots merged in integers, rounded once (finalize_x64_block).
+__global__ void __launch_bounds__(kFinalThreads) finalize_x64_kernel(const XPart* __restrict__ partial,
+                                                                     const FpFinal* __restrict__ f,
+                                                                     int cplx, void* __restrict__ out) {
+    __shared__ XFinSh sh;
+    finalize_x64_block(partial, f[blockIdx.x], cplx, out, sh);
+}
 
 // Server variant: accumulators and outputs at arbitrary indices.
 __global__ void finalize_modp_at_kernel(const unsigned long long* __restrict__ acc, const ModpFinalAt* __restrict__ f,
@@ -342,10 +349,14 @@ cudaError_t launch_stage_x64(bool cplx, const void* A, const StageDesc* d, int64
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
-                               cudaStream_t s) {
+cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, bool x64,
+                               void* out, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    finalize_fp_kernel<<<(unsigned)count, kFinalThreads, 0, s>>>(partial, f, cplx ? 1 : 0, out);
+    if (x64)
+        finalize_x64_kernel<<<(unsigned)count, kFinalThreads, 0, s>>>(reinterpret_cast<const XPart*>(partial), f,
+                                                                      cplx ? 1 : 0, out);
+    else
+        finalize_fp_kernel<<<(unsigned)count, kFinalThreads, 0, s>>>(partial, f, cplx ? 1 : 0, out);
     return cudaGetLastError();
 }
 
@@ -553,7 +564,7 @@ int prepare_batch(Field field, const int32_t* n, const int64_t* offset, const ui
                 fin[m].out_index = b;
             }
         }
-        const int pw = cplx ? 4 : 2;   // doubles per partial
+        const int pw = fp_slot_doubles(!X.P.groups.empty() && X.P.groups[0].x64, cplx);   // doubles per partial slot
         X.o_stage = 0;
         X.o_fin = align256(sizeof(StageDesc) * batch);
         X.o_meta_end = align256(X.o_fin + sizeof(FpFinal) * batch);
@@ -779,7 +790,7 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
         return PERMX_OK;
     }
     const bool cplx = X.field == Field::C128;
-    const int pw = cplx ? 4 : 2;
+    const int pw = fp_slot_doubles(X.x64, cplx);
     const FpFinal* fin = reinterpret_cast<const FpFinal*>(d + X.o_fin);
     const double* part = reinterpret_cast<const double*>(d + X.o_part);
     if (e == cudaSuccess)
@@ -807,8 +818,7 @@ int execute_batch(const Prepared& X, const void* A, void* out, cudaStream_t s) {
             if (g.x64) f = cplx ? dispatch_x64c(g.n, L, ls) : dispatch_x64r(g.n, L, ls);
             else f = cplx ? dispatch_c128(g.n, L, ls) : dispatch_f64(g.n, L, ls);
             if (f != cudaSuccess || fused) return f;
-            finalize_fp_kernel<<<(unsigned)count, kFinalThreads, 0, ls>>>(part, fin + g.first_mat, cplx ? 1 : 0, out);
-            return cudaGetLastError();
+            return launch_finalize_fp(part, fin + g.first_mat, count, cplx, g.x64, out, ls);
         });
     if (e != cudaSuccess) return cuda_fail(e, cplx ? "perm_c128 launch" : "perm_f64 launch");
     return PERMX_OK;

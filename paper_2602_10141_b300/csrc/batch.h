@@ -94,7 +94,7 @@ cudaError_t launch_stage(int field, const void* A, const StageDesc* d, int64_t c
 cudaError_t launch_stage_x64(bool cplx, const void* A, const StageDesc* d, int64_t count, void* colT,
                              cudaStream_t s);
 int set_fp_arith(int mode);
-cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, void* out,
+cudaError_t launch_finalize_fp(const double* partial, const FpFinal* f, int64_t count, bool cplx, bool x64, void* out,
                                cudaStream_t s);
 cudaError_t launch_finalize_modp_at(const unsigned long long* acc, const ModpFinalAt* f, int64_t count, uint32_t* out,
                                     cudaStream_t s);

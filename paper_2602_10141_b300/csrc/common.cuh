@@ -83,6 +83,21 @@ struct ModpFinal {
     int32_t pad_;
     int64_t out_index;
 };
+// Integer-mode partial of one chunk lane group and component: the group's
+// exact 128-bit fixed-point sum (hi:lo) * 2^e, the matrix's staging scale
+// included in e.  flag: 0 no term, 1 a sum, 2 the matrix has a non-finite
+// entry.  The finalisation merges these in integers and rounds once.
+struct alignas(16) XPart {
+    uint64_t lo;
+    int64_t hi;
+    int32_t e;
+    int32_t flag;
+    int64_t pad;
+};
+// doubles per partial slot: FP64 mode (sum, compensation) per component,
+// integer mode one XPart per component
+constexpr int fp_slot_doubles(bool x64, bool cplx) { return x64 ? (cplx ? 8 : 4) : (cplx ? 4 : 2); }
+
 struct FpFinal {
     int64_t first, count;   // partial slots of this matrix
     int64_t out_index;

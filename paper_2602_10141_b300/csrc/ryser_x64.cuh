@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
     for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          base < L.item_end; base += stride) {
         const uint64_t item = base + lane;
-        double s = 0.0, comp = 0.0;
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
@@ -133,13 +132,9 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
             }
         }
         x64_group_merge(acc, G);
-        if ((lane & (G - 1)) == 0 && valid) {
-            x64_acc_to_dd(acc, scale, s, comp);
-            if (nonfinite) s = comp = __longlong_as_double(0x7ff8000000000000ll);
-            reinterpret_cast<double2*>(L.partial)[slot] = make_double2(s, comp);
-        }
+        if ((lane & (G - 1)) == 0 && valid) reinterpret_cast<XPart*>(L.partial)[slot] = x64_part(acc, scale, nonfinite);
     }
-    if (L.fin) fused_finalize_fp(L);
+    if (L.fin) fused_finalize_x64(L);
 }
 
 template <int N>
@@ -152,7 +147,6 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
     for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          base < L.item_end; base += stride) {
         const uint64_t item = base + lane;
-        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
@@ -217,15 +211,12 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
         x64_group_merge(ar, G);
         x64_group_merge(ai, G);
         if ((lane & (G - 1)) == 0 && valid) {
-            x64_acc_to_dd(ar, scale, sr, cr);
-            x64_acc_to_dd(ai, scale, si, ci);
-            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
-            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
-            out[0] = make_double2(sr, cr);
-            out[1] = make_double2(si, ci);
+            XPart* out = reinterpret_cast<XPart*>(L.partial) + 2 * slot;
+            out[0] = x64_part(ar, scale, nonfinite);
+            out[1] = x64_part(ai, scale, nonfinite);
         }
     }
-    if (L.fin) fused_finalize_fp(L);
+    if (L.fin) fused_finalize_x64(L);
 }
 
 // Complex rows wider than 16: two lanes share a chunk.  Lane h of a pair
@@ -249,7 +240,6 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
     for (uint64_t base = L.item_begin + ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 2;
          base < L.item_end; base += stride) {
         const uint64_t item = base + (lane >> 1);
-        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
@@ -346,15 +336,12 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         }
         const XAcc ar = acc;
         if ((lane & (2 * G - 1)) == 0 && valid) {
-            x64_acc_to_dd(ar, scale, sr, cr);
-            x64_acc_to_dd(ai, scale, si, ci);
-            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
-            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
-            out[0] = make_double2(sr, cr);
-            out[1] = make_double2(si, ci);
+            XPart* out = reinterpret_cast<XPart*>(L.partial) + 2 * slot;
+            out[0] = x64_part(ar, scale, nonfinite);
+            out[1] = x64_part(ai, scale, nonfinite);
         }
     }
-    if (L.fin) fused_finalize_fp(L);
+    if (L.fin) fused_finalize_x64(L);
 }
 
 // Four lanes per chunk (complex, 8 <= n <= 16), for launches too small to
@@ -406,7 +393,6 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
     for (uint64_t base = L.item_begin + (uint64_t)blockIdx.x * 32; base < L.item_end;
          base += (uint64_t)gridDim.x * 32) {
         const uint64_t item = base + cl;
-        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
         bool valid = item < L.item_end;
         const double* cold = L.colT;
         uint64_t c = 0, slot = 0;
@@ -515,15 +501,12 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
             x64_acc_merge(ai, bi);
         }
         if (q == 0 && (cl & (G - 1)) == 0 && valid) {
-            x64_acc_to_dd(ar, scale, sr, cr);
-            x64_acc_to_dd(ai, scale, si, ci);
-            if (nonfinite) sr = cr = si = ci = __longlong_as_double(0x7ff8000000000000ll);
-            double2* out = reinterpret_cast<double2*>(L.partial) + 2 * slot;
-            out[0] = make_double2(sr, cr);
-            out[1] = make_double2(si, ci);
+            XPart* out = reinterpret_cast<XPart*>(L.partial) + 2 * slot;
+            out[0] = x64_part(ar, scale, nonfinite);
+            out[1] = x64_part(ai, scale, nonfinite);
         }
     }
-    if (L.fin) fused_finalize_fp(L);
+    if (L.fin) fused_finalize_x64(L);
 }
 
 template <int N>

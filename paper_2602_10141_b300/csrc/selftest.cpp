@@ -27,6 +27,14 @@ int permx_x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int32_t sh,
 
 int64_t permx_x64_scaled_round(double a, int32_t k) { return x64_scaled_round(a, k); }
 
+double permx_x64_to_double(int64_t hi, uint64_t lo, int32_t e) {
+    XAcc a;
+    a.acc = (__int128)(((unsigned __int128)(uint64_t)hi << 64) | lo);
+    a.E = e;
+    a.set = true;
+    return x64_acc_to_double(a, 0);
+}
+
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {
     if (!R || !m_out || !e_out || n < 1 || n > 64) return -1;
     XReal t[4];

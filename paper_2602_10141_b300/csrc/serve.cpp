@@ -179,7 +179,7 @@ void plan_request(Request* r, bool x64) {
     r->ld = modp ? pad4(r->n) : r->field == PERMX_FIELD_F64 ? pad2(r->n) : r->n;
     // staged columns (plus the x column); the integer-mantissa layout adds a scale word pair
     r->col_bytes = align256((size_t)(r->n + 1) * r->ld * entry_bytes(r->field) + (r->x64 ? 16 : 0));
-    const size_t tail = modp ? 8 : (size_t)(r->chunks >> r->lg) * (r->field == PERMX_FIELD_C128 ? 32 : 16);
+    const size_t tail = modp ? 8 : (size_t)(r->chunks >> r->lg) * 8 * fp_slot_doubles(r->x64, r->field == PERMX_FIELD_C128);
     r->bytes = r->col_bytes + align256(tail);
     r->cost = (double)r->n * std::ldexp(1.0, bits) * term_cost(r->field, r->x64);
 }
@@ -307,7 +307,7 @@ int enqueue_step(perm_server* S, StepBuf& B, int slot, const std::vector<Request
                 d.p = r->p;
                 d.pinv = inv_mod_2_32(r->p);
             } else {
-                d.out_off = (r->arena_off + (int64_t)r->col_bytes) / (r->field == PERMX_FIELD_C128 ? 32 : 16);
+                d.out_off = (r->arena_off + (int64_t)r->col_bytes) / (8 * fp_slot_doubles(r->x64, r->field == PERMX_FIELD_C128));
             }
             segs.push_back(d);
             item += grant[i];
@@ -338,7 +338,7 @@ int enqueue_step(perm_server* S, StepBuf& B, int slot, const std::vector<Request
             fm.push_back(x);
             om.push_back(r);
         } else {
-            const int pw = r->field == PERMX_FIELD_C128 ? 4 : 2;
+            const int pw = fp_slot_doubles(r->x64, r->field == PERMX_FIELD_C128);
             FpFinal x{};
             x.first = (r->arena_off + (int64_t)r->col_bytes) / (8 * pw);
             x.count = (int64_t)(r->chunks >> r->lg);
@@ -470,10 +470,10 @@ int enqueue_step(perm_server* S, StepBuf& B, int slot, const std::vector<Request
                                            reinterpret_cast<uint32_t*>(dres + r_m), st));
         PERMX_CUDA(launch_finalize_fp(reinterpret_cast<const double*>(S->arena_base),
                                       reinterpret_cast<const FpFinal*>(B.d_meta + o_fc), (int64_t)fc.size(), true,
-                                      dres + r_c, st));
+                                      S->x64, dres + r_c, st));
         PERMX_CUDA(launch_finalize_fp(reinterpret_cast<const double*>(S->arena_base),
                                       reinterpret_cast<const FpFinal*>(B.d_meta + o_ff), (int64_t)ff.size(), false,
-                                      dres + r_f, st));
+                                      S->x64, dres + r_f, st));
         S->launches += (!fm.empty()) + (!fc.empty()) + (!ff.empty());
         PERMX_CUDA(cudaMemcpyAsync(B.h_meta + o_res, dres, total - 256 - o_res, cudaMemcpyDeviceToHost, st));
         for (size_t i = 0; i < oc.size(); ++i) B.results.push_back({oc[i], o_res + r_c + 16 * i});

@@ -4,6 +4,9 @@
 #pragma once
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
 
 #if !defined(__CUDACC__) && !defined(__host__)
 #define __host__
@@ -306,6 +309,68 @@ __host__ __device__ __forceinline__ void x64_acc_merge(XAcc& a, const XAcc& b) {
     const int E = a.E > b.E ? a.E : b.E;
     a.acc = x64_sar128(a.acc, E - a.E) + x64_sar128(b.acc, E - b.E);
     a.E = E;
+}
+
+// The double nearest to acc * 2^(E + extra), ties to even, in integer
+// operations only (B300's FP64 latency makes a handful of FP64 operations cost
+// more than the whole conversion): the one rounding of an exact sum.
+// Subnormal results are rounded once at their own precision; too large ones
+// give +-inf.
+__host__ __device__ __forceinline__ double x64_acc_to_double(const XAcc& a, int extra) {
+    if (!a.set || a.acc == 0) return 0.0;
+    const bool neg = a.acc < 0;
+    const unsigned __int128 m = neg ? (unsigned __int128)0 - (unsigned __int128)a.acc : (unsigned __int128)a.acc;
+    const uint64_t mh = (uint64_t)(m >> 64), ml = (uint64_t)m;
+    const int b = mh ? 127 - x64_clz(mh) : 63 - x64_clz(ml);   // top bit of m
+    const int F = a.E + extra;                                 // the value is m * 2^F
+    int lsb = F + b - 52;                                      // lowest bit of a 53-bit significand
+    if (lsb < -1074) lsb = -1074;
+    const int sh = lsb - F;
+    uint64_t q;
+    if (sh <= 0) {
+        q = (uint64_t)(m << (-sh));                            // exact, below 2^53
+    } else if (sh > 128) {
+        q = 0;                                                 // below half the smallest subnormal
+    } else if (sh == 128) {
+        q = m > ((unsigned __int128)1 << 127) ? 1 : 0;
+    } else {
+        q = (uint64_t)(m >> sh);
+        const unsigned __int128 rem = m - ((unsigned __int128)q << sh), half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+    }
+    if (q >> 53) {                                             // rounded up to 2^53
+        q >>= 1;
+        ++lsb;
+    }
+    uint64_t bits;
+    if (q >= (1ull << 52) && lsb + 1075 >= 2047) bits = 0x7ff0000000000000ull;   // overflow
+    else bits = ((uint64_t)(lsb + 1074) << 52) + q;            // normal or subnormal (lsb = -1074)
+    if (neg) bits |= 0x8000000000000000ull;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+#endif
+}
+
+// A lane group's sum as the partial it leaves for the finalisation
+__host__ __device__ __forceinline__ XPart x64_part(const XAcc& a, int scale, bool nonfinite) {
+    XPart p;
+    p.lo = (uint64_t)a.acc;
+    p.hi = (int64_t)(a.acc >> 64);
+    p.e = a.E + scale;
+    p.flag = nonfinite ? 2 : (a.set ? 1 : 0);
+    p.pad = 0;
+    return p;
+}
+__host__ __device__ __forceinline__ XAcc x64_acc_of_part(const XPart& p) {
+    XAcc a;
+    a.acc = (__int128)(((unsigned __int128)(uint64_t)p.hi << 64) | p.lo);
+    a.E = p.e;
+    a.set = p.flag == 1;
+    return a;
 }
 
 // acc * 2^(E + scale) as a double-double (hi + lo)

@@ -2,6 +2,7 @@
 the CPU through the library's self-test hooks (the same inline functions the
 kernels use) and checked against exact Python integers and fractions."""
 import ctypes
+import math
 import os
 import random
 from fractions import Fraction
@@ -257,3 +258,38 @@ def test_scaled_round_is_exact_round_half_even(lib):
             d = x - fl
             want = fl + 1 if d > Fraction(1, 2) or (d == Fraction(1, 2) and fl % 2) else fl
             assert f(a, k) == want, (a, k)
+
+
+def test_integer_rounding_to_double_is_correctly_rounded(lib):
+    """The finalisation's single rounding: (hi:lo) * 2^e to the nearest double,
+    ties to even, against Python's correctly rounded Fraction -> float, over
+    normal, subnormal and overflowing results and exact ties."""
+    lib.permx_x64_to_double.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32]
+    lib.permx_x64_to_double.restype = ctypes.c_double
+    rnd = random.Random(11)
+
+    def expect(v, e):
+        try:
+            return float(Fraction(v) * Fraction(2) ** e)
+        except OverflowError:
+            return math.inf if v > 0 else -math.inf
+
+    cases = []
+    for _ in range(4000):
+        bits = rnd.randint(1, 126)
+        v = rnd.getrandbits(bits) * rnd.choice((-1, 1))
+        e = rnd.choice((rnd.randint(-200, 200), rnd.randint(-1300, -1000), rnd.randint(900, 1100)))
+        cases.append((v, e))
+    # exact ties at the 53-bit boundary, odd and even significands, and the carry to 2^53
+    for sig in (2 ** 52, 2 ** 52 + 1, 2 ** 53 - 1):
+        for sh in (1, 2, 11, 70):
+            cases.append(((2 * sig + 1) << (sh - 1), -sh))
+    cases += [((2 ** 53 - 1) * 2 + 1, 0), (1, -1074), (1, -1075), (3, -1076), (1, -1076), (2 ** 127 - 1, 1000),
+              (-(2 ** 127), -1200), (1, 1023), (2 ** 53 - 1, 971), (2 ** 53 - 1, 972)]
+    for v, e in cases:
+        if v == 0:
+            continue
+        hi, lo = (v >> 64), v & (2 ** 64 - 1)
+        got = lib.permx_x64_to_double(hi, lo, e)
+        want = expect(v, e)
+        assert got == want and math.copysign(1.0, got) == math.copysign(1.0, want), (v, e, got, want)
