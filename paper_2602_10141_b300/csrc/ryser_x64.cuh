@@ -20,8 +20,10 @@
 //    factor;
 //  - each chunk adds its terms into a 128-bit fixed-point accumulator whose
 //    grid follows the chunk's first term (error at most 2^-80 of the sum of
-//    the term magnitudes), and hands the chunk total on as a double-double
-//    scaled back by 2^-sum(sigma).
+//    the term magnitudes); lane groups merge their chunk sums in integers and
+//    leave one 128-bit partial per group (XPart, with the staging scale
+//    2^-sum(sigma) in its exponent), which the finalisation merges the same
+//    way and rounds to double once.
 // The result is therefore not exact; relative precision per factor is about
 // 2^-58 (float64: 2^-53), and the tests check these bounds against exact
 // rational arithmetic.
@@ -33,9 +35,8 @@
 namespace permx {
 
 // Reduction of the lanes' chunk accumulators over aligned groups of
-// `lanes` lanes (xor butterfly of symmetric merges), in integers: the
-// double-double conversion then happens once per group instead of once per
-// chunk, which keeps the slow FP64 pipe out of the per-chunk path.
+// `lanes` lanes (xor butterfly of symmetric merges), in integers, which keeps
+// the slow FP64 pipe out of the walk altogether.
 __device__ __forceinline__ void x64_group_merge(XAcc& a, int lanes, int first = 1) {
     for (int d = first; d < lanes; d <<= 1) {
         XAcc b;

@@ -373,7 +373,8 @@ __host__ __device__ __forceinline__ XAcc x64_acc_of_part(const XPart& p) {
     return a;
 }
 
-// acc * 2^(E + scale) as a double-double (hi + lo)
+// acc * 2^(E + scale) as a double-double (hi + lo): the host self-test's view
+// of an accumulator (the kernels use x64_acc_to_double at the finalisation)
 __host__ __device__ __forceinline__ void x64_acc_to_dd(const XAcc& a, int scale, double& hi, double& lo) {
     if (!a.set || a.acc == 0) {
         hi = 0.0;
