@@ -417,43 +417,49 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
                     Ri[k] = x.y;
                 }
             }
+            // a lone matrix runs one warp per SM sub-partition, so latency is
+            // the cost: every column's loads are issued at once (no branch on
+            // the subset bits; a column outside S0 adds 0), and each step's
+            // column is loaded one step ahead
             const uint64_t S0 = ks ^ (ks >> 1);
-#pragma unroll 1
+#pragma unroll
             for (int j = 0; j < N; ++j) {
-                if (!((S0 >> j) & 1)) continue;
+                const int64_t in = -(int64_t)((S0 >> j) & 1);
 #pragma unroll
                 for (int k = 0; k < RQ; ++k) {
                     if (q + 4 * k < N) {
                         const longlong2 v = __ldg(col + j * N + q + 4 * k);
-                        Rr[k] += v.x;
-                        Ri[k] += v.y;
+                        Rr[k] += v.x & in;
+                        Ri[k] += v.y & in;
                     }
                 }
             }
             scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
             nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
+            longlong2 nxt[RQ];                       // column of the step into k + 1
+#pragma unroll
+            for (int r = 0; r < RQ; ++r) nxt[r] = make_longlong2(0, 0);
+            if (ks + 1 < ke) {
+                const int j = __ffsll((long long)(ks + 1)) - 1;
+#pragma unroll
+                for (int r = 0; r < RQ; ++r)
+                    if (q + 4 * r < N) nxt[r] = __ldg(col + j * N + q + 4 * r);
+            }
             for (uint64_t k = ks; k < ke; ++k) {
                 if (k > ks) {
                     const int j = __ffsll((long long)k) - 1;
-                    const longlong2* cj = col + j * N + q;
-                    if ((k >> (j + 1)) & 1) {
+                    const int64_t neg = -(int64_t)((k >> (j + 1)) & 1);   // the column leaves S
 #pragma unroll
-                        for (int r = 0; r < RQ; ++r) {
-                            if (q + 4 * r < N) {
-                                const longlong2 v = __ldg(cj + 4 * r);
-                                Rr[r] -= v.x;
-                                Ri[r] -= v.y;
-                            }
-                        }
-                    } else {
+                    for (int r = 0; r < RQ; ++r) {
+                        // +v or -v: (v ^ neg) - neg
+                        Rr[r] += (nxt[r].x ^ neg) - neg;
+                        Ri[r] += (nxt[r].y ^ neg) - neg;
+                    }
+                    if (k + 1 < ke) {
+                        const int jn = __ffsll((long long)(k + 1)) - 1;
 #pragma unroll
-                        for (int r = 0; r < RQ; ++r) {
-                            if (q + 4 * r < N) {
-                                const longlong2 v = __ldg(cj + 4 * r);
-                                Rr[r] += v.x;
-                                Ri[r] += v.y;
-                            }
-                        }
+                        for (int r = 0; r < RQ; ++r)
+                            if (q + 4 * r < N) nxt[r] = __ldg(col + jn * N + q + 4 * r);
                     }
                 }
                 // chain q (rows q, q+4, q+8, ...), as the one-lane kernel forms t[q]

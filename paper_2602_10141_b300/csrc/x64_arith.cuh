@@ -285,10 +285,14 @@ __host__ __device__ __forceinline__ void x64_acc_add(XAcc& a, int64_t m, int e, 
         a.E += d;
         sh = 40;
     }
-    __int128 v;
-    if (sh >= 0) v = (__int128)m << sh;
-    else if (sh > -63) v = (__int128)(m >> (-sh));
-    else return;
+    if (sh <= -63) return;
+    // v = m 2^sh (sh in [0, 40]) or floor(m 2^sh) (sh in (-63, 0)) as two 64-bit
+    // words: a 64-bit shift and a sign or funnel word instead of a general
+    // 128-bit variable shift (same value)
+    const int64_t ms = sh >= 0 ? m : (m >> (-sh));
+    const uint64_t vl = sh > 0 ? (uint64_t)m << sh : (uint64_t)ms;
+    const int64_t vh = sh > 0 ? (m >> (64 - sh)) : (ms >> 63);
+    const __int128 v = (__int128)(((unsigned __int128)(uint64_t)vh << 64) | vl);
     a.acc = negate ? a.acc - v : a.acc + v;
 }
 // a <- a + b, both aligned to the larger exponent (the smaller-exponent one
