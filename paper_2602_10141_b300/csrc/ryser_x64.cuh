@@ -319,8 +319,11 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 o.im = (int64_t)__shfl_xor_sync(pair_mask, (long long)p.im, 1);
                 o.e = __shfl_xor_sync(pair_mask, p.e, 1);
                 const XCplx a = h ? o : p, b = h ? p : o;
-                const XCplx t2 = x64c_mul(a, b.re, b.im, b.e);
-                x64_acc_add(acc, h ? t2.im : t2.re, t2.e, k & 1);
+                // each lane forms only the component it accumulates, un-normalised:
+                // Re = k1 - k3, Im = k1 + k2 (the Karatsuba products of x64c_mulhi)
+                const int64_t k1 = x64_mulhi62(a.re + a.im, b.re);
+                const int64_t kx = x64_mulhi62(h ? a.re : a.im, h ? b.im - b.re : b.re + b.im);
+                x64_acc_add(acc, h ? k1 + kx : k1 - kx, a.e + b.e + 62, k & 1);
             }
         }
         // merge even lanes with even lanes (Re) and odd with odd (Im), then the
