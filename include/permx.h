@@ -85,8 +85,9 @@ const char* permx_version(void);
  * sums R of the rounded, scaled matrix are exact int64 values (|R_i| < 2^62 + n);
  * each term multiplies its n row sums with truncated 62-bit integer mantissas
  * (error at most 16n (real) or 64n (complex) times sum_i |R_i|^-1 prod_k |R_k|,
- * about 2^-58 sum_j |a_ij| / |r_i| relative per factor for the unscaled row
- * sum r_i); each chunk adds its terms
+ * a chain's head row sum counting as 2^62 in its first factor; about 2^-58
+ * sum_j |a_ij| / |r_i| relative per factor for the unscaled row sum r_i); each
+ * chunk adds its terms
  * in 128-bit fixed point (error at most 2^-80 of the sum of the term
  * magnitudes), and the chunk sums are merged in integers (the same 2^-80
  * grid rule) and rounded to float64 once.  The result is not exact: it is

@@ -13,11 +13,12 @@
 //    [2^61, 2^62 + 2^10]; complex: |Re m| + |Im m| <= 2^62 + 2^10) and an int
 //    exponent.  A chain factor is m R >> 64, a combining factor m m' >> 62,
 //    each one truncated 64x64 -> 128-bit product from three signed
-//    32x32 -> 64-bit multiplies, then a leading-zero normalisation (a chain
-//    that is a single row sum enters the combining products as R itself), so
-//    a term carries a truncation error of at most 16n times
-//    sum_i prod_{k != i} |R_k| (complex: 64n), i.e. about 2^-58 relative per
-//    factor;
+//    32x32 -> 64-bit multiplies, then a leading-zero normalisation (a chain's
+//    head row sum enters its first chain factor as it is, exponent 0, and a
+//    chain that is a single row sum enters the combining products as R
+//    itself), so a term carries a truncation error of at most 16n times
+//    sum_i prod_{k != i} |R_k| (complex: 64n; in a chain's first factor the
+//    head counts as 2^62), i.e. about 2^-58 relative per factor;
 //  - each chunk adds its terms into a 128-bit fixed-point accumulator whose
 //    grid follows the chunk's first term (error at most 2^-80 of the sum of
 //    the term magnitudes); lane groups merge their chunk sums in integers and
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
                 // four interleaved product chains, then combined
                 XReal t[4];
 #pragma unroll
-                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64_from_int(R[q]);
+                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64_head(R[q], q + 4 >= N);
 #pragma unroll
                 for (int i = 4; i < N; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
                 const XReal p = x64_term(t, N);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
                 }
                 XCplx t[4];
 #pragma unroll
-                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+                for (int q = 0; q < 4 && q < N; ++q) t[q] = x64c_head(Rr[q], Ri[q], q + 4 >= N);
 #pragma unroll
                 for (int i = 4; i < N; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
                 const XCplx p = x64c_term(t, N);
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
                 // the lane's half product (rows >= 4 for n >= 8, so all four chains start)
                 XCplx t[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+                for (int q = 0; q < 4; ++q) t[q] = x64c_head(Rr[q], Ri[q], q + 4 >= N - H);
 #pragma unroll
                 for (int i = 4; i < H; ++i)
                     if (i < rows) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
                     }
                 }
                 // chain q (rows q, q+4, q+8, ...), as the one-lane kernel forms t[q]
-                XCplx t = x64c_from_int(Rr[0], Ri[0]);
+                XCplx t = x64c_head(Rr[0], Ri[0], q + 4 >= N);
 #pragma unroll
                 for (int r = 1; r < RQ; ++r)
                     if (q + 4 * r < N) t = x64c_mul_row(t, Rr[r], Ri[r]);

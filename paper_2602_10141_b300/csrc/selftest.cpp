@@ -38,7 +38,7 @@ double permx_x64_to_double(int64_t hi, uint64_t lo, int32_t e) {
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out) {
     if (!R || !m_out || !e_out || n < 1 || n > 64) return -1;
     XReal t[4];
-    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64_from_int(R[q]);
+    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64_head(R[q], q + 4 >= n);
     for (int i = 4; i < n; ++i) t[i & 3] = x64_mul_row(t[i & 3], R[i]);
     const XReal p = x64_term(t, n);
     *m_out = p.m;
@@ -50,7 +50,7 @@ int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t*
                        int32_t* e_out) {
     if (!Rr || !Ri || !re_out || !im_out || !e_out || n < 1 || n > 64) return -1;
     XCplx t[4];
-    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64c_from_int(Rr[q], Ri[q]);
+    for (int q = 0; q < 4 && q < n; ++q) t[q] = x64c_head(Rr[q], Ri[q], q + 4 >= n);
     for (int i = 4; i < n; ++i) t[i & 3] = x64c_mul_row(t[i & 3], Rr[i], Ri[i]);
     const XCplx p = x64c_term(t, n);
     *re_out = p.re;

@@ -195,6 +195,14 @@ __host__ __device__ __forceinline__ XReal x64_from_int(int64_t r) {
     const int s = x64_norm_shift_top<62>(x64_top_hi(r));
     return XReal{x64_shl(r, s), -s};
 }
+// The head of a product chain: a staged row sum (|R| < 2^62 + n) is already a
+// valid chain-factor operand, so it enters as it is (exponent 0) when a chain
+// factor follows (norm = false): that factor then truncates on the row sum's
+// own grid, as if the head were 2^62 in size, which the error bound counts.
+// A chain that is only its head goes to the combining products normalised.
+__host__ __device__ __forceinline__ XReal x64_head(int64_t R, bool norm) {
+    return norm ? x64_from_int(R) : XReal{R, 0};
+}
 __host__ __device__ __forceinline__ XReal x64_mul(XReal a, int64_t m2, int e2) {
     const int64_t x = x64_mulhi62(a.m, m2);
     const int s = x64_norm_shift_top<62>(x64_top_hi(x));
@@ -213,6 +221,9 @@ __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) 
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), -s};
+}
+__host__ __device__ __forceinline__ XCplx x64c_head(int64_t re, int64_t im, bool norm) {
+    return norm ? x64c_from_int(re, im) : XCplx{re, im, 0};
 }
 // (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^10: the combining factor
 __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t bi, int eb) {

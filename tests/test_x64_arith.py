@@ -96,12 +96,20 @@ def _error_scale(R):
     """sum_i 2^61 prod_{k != i} max(|R_k|, 2^32): the size one truncation per factor
     can reach.  Normalisation looks at the high 32-bit word only, so a factor below
     2^32 (a row sum cancelling to 2^-29 of its row's scale) counts as 2^32; such a
-    term is itself that much below typical terms."""
+    term is itself that much below typical terms.  A chain's head row sum enters
+    its first chain factor un-normalised (factor i = q + 4 for head q), which
+    truncates as if the head were 2^62 in size: that factor's share counts the
+    head as max(|R_q|, 2^62)."""
+    n = len(R)
     tot = 0
-    for i in range(len(R)):
+    for i in range(n):
         p = 2 ** 61
         for k, r in enumerate(R):
-            if k != i:
+            if k == i:
+                continue
+            if 4 <= i < 8 and k == i - 4:
+                p *= max(abs(r), 2 ** 62)
+            else:
                 p *= max(abs(r), 2 ** 32)
         tot += p
     return tot
