@@ -3,6 +3,7 @@ multiply-adds) against the host forms of the same functions (bit for bit) and
 against exact integers (the truncation bound), over the operand ranges the
 float walks use."""
 import ctypes
+import math
 import random
 
 import numpy as np
@@ -110,3 +111,56 @@ def test_complex_products_match_host_and_bound(lib):
         assert lib.permx_x64c_mulhi(ar, ai, br, bi, 62, ctypes.byref(re), ctypes.byref(im)) == 0
         assert (out[k, 2], out[k, 3]) == (re.value, im.value)
         assert -4 <= re.value - (er >> 62) <= 4 and -4 <= im.value - (ei >> 62) <= 4
+
+
+def _perm_batch(mats):
+    """Integer-mode permanents of a list of equal-size matrices (one call)."""
+    import torch
+    import paper_2602_10141_b300 as px
+    n = mats[0].shape[0]
+    flat = np.ascontiguousarray(np.stack(mats)).reshape(-1)
+    cplx = np.iscomplexobj(flat)
+    A = torch.from_numpy(flat.view(np.float64) if cplx else flat).cuda()
+    if cplx:
+        A = A.view(torch.complex128)
+    out = torch.empty(len(mats), dtype=torch.complex128 if cplx else torch.float64, device="cuda")
+    (px.perm_c128 if cplx else px.perm_f64)(A, [n] * len(mats), [i * n * n for i in range(len(mats))], out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_power_of_two_scaling_is_exact_through_the_final_rounding(cplx):
+    """Scaling every entry by 2^k moves each row scale by -k and leaves the
+    staged integers, the walk and the exact sums unchanged, so the single final
+    rounding gives exactly perm(A) 2^(n k) while that stays a normal double;
+    in the subnormal range the result is within one subnormal step of it, and
+    past the top of the range it is +-inf."""
+    import paper_2602_10141_b300 as px
+    old = px.permx_set_fp_arith(1)
+    try:
+        g = np.random.default_rng(21)
+        n = 8
+        if cplx:
+            A = (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))) / np.sqrt(2)
+        else:
+            A = g.standard_normal((n, n))
+        ks = [0, -100, -60, 40, 100, -132, -134, 130]
+        got = _perm_batch([A * 2.0 ** k for k in ks])
+        base = got[0]
+        assert abs(base) > 2.0 ** -10
+        parts = (lambda z: (z.real, z.imag)) if cplx else (lambda z: (z,))
+        for k, v in zip(ks, got):
+            for b, x in zip(parts(base), parts(v)):
+                try:
+                    want = math.ldexp(float(b), n * k)
+                except OverflowError:
+                    want = math.copysign(math.inf, b)
+                if math.isinf(want):
+                    assert x == want, (k, x)
+                elif abs(want) >= 2.0 ** -1022:
+                    assert x == want, (k, x, want)
+                else:
+                    assert abs(x - want) <= 2.0 ** -1074, (k, x, want)
+    finally:
+        px.permx_set_fp_arith(old)
