@@ -206,18 +206,28 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             // products are formed from independent arrays, which doubles the
             // instruction-level parallelism of the product trees.  r2 is
             // computed from r and the next r from r2, so no array is copied.
+            // A pair's two products are added to E and O one pair later, so no
+            // instruction of the pair waits for the trees' last levels and the
+            // next pair's column steps and trees issue behind them.
+            mont_t pe = 0, po = 0;
             while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke) {
                 uint32_t r2[N];
                 if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
                 else column_step<N, false>(r2, r, col, p, z0);
-                E += prod_tree<N>(r, p, pinv, (int32_t)z0);
-                O += prod_tree<N>(r2, p, pinv, (int32_t)z0);
+                const mont_t te = prod_tree<N>(r, p, pinv, (int32_t)z0);
+                const mont_t to = prod_tree<N>(r2, p, pinv, (int32_t)z0);
+                E += pe;
+                O += po;
+                pe = te;
+                po = to;
                 k += 2;
                 if (k >= ke) break;          // the chunk is done; r is not needed again
                 const int j = __ffsll((long long)k) - 1;
                 if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p, z0);
                 else column_step<N, false>(r, r2, col + j * NP, p, z0);
             }
+            E += pe;
+            O += po;
             for (; k < ke; ++k) {              // remaining steps one at a time
                 if (k & 1) O += prod_tree<N>(r, p, pinv, (int32_t)z0); else E += prod_tree<N>(r, p, pinv, (int32_t)z0);
                 if (k + 1 < ke) toggle_column<N>(r, col, k + 1, p);
