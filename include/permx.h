@@ -82,7 +82,7 @@ const char* permx_version(void);
  * (default) runs on the integer pipes.  Row i is scaled by a power of two
  * 2^s_i with 2^s_i sum_j |a_ij| in [2^62, 2^63) and its entries rounded to even
  * integers (each entry moves by at most 2^-62 sum_j |a_ij|), so the walk's row
- * sums R of the rounded, scaled matrix are exact int64 values (|R_i| < 2^62 + n);
+ * sums R of the rounded, scaled matrix are exact int64 values (|R_i| < 2^62 + 2^17);
  * each term multiplies its n row sums with truncated 62-bit integer mantissas
  * (error at most 16n (real) or 64n (complex) times sum_i |R_i|^-1 prod_k |R_k|,
  * a chain's head row sum counting as 2^62 in its first factor; about 2^-58

@@ -30,7 +30,7 @@ int permx_x64_mulhi_device(const int64_t* a, const int64_t* b, int64_t count, in
 
 /* Complex product (ar + i ai)(br + i bi) >> sh by components (sh = 64: the
  * walks' chain factor; sh = 62: the combining factor), for
- * |ar| + |ai|, |br| + |bi| <= 2^62 + 2^10: Karatsuba on the truncated products
+ * |ar| + |ai|, |br| + |bi| <= 2^62 + 2^20: Karatsuba on the truncated products
  * above, each component within 4 of the exact value.  Returns PERMX_EINVAL for
  * another sh or a NULL output. */
 int permx_x64c_mulhi(int64_t ar, int64_t ai, int64_t br, int64_t bi, int32_t sh, int64_t* re, int64_t* im);
@@ -50,11 +50,11 @@ double permx_x64_to_double(int64_t hi, uint64_t lo, int32_t e);
  * float entry to the integer-mantissa walk's format (finite a, |a 2^k| < 2^62). */
 int64_t permx_x64_scaled_round(double a, int32_t k);
 
-/* Product of n exact integer row sums R[0..n) (|R| < 2^62 + n) as the real walk
+/* Product of n exact integer row sums R[0..n) (|R| < 2^62 + 2^17) as the real walk
  * forms it (four interleaved chains, then combined): value m * 2^e. */
 int permx_x64_product(const int64_t* R, int32_t n, int64_t* m_out, int32_t* e_out);
 
-/* Complex version: rows (Rr[i] + i Ri[i]), |Rr[i]| + |Ri[i]| < 2^62 + 64;
+/* Complex version: rows (Rr[i] + i Ri[i]), |Rr[i]| + |Ri[i]| < 2^62 + 2^17;
  * value (re + i im) * 2^e. */
 int permx_x64c_product(const int64_t* Rr, const int64_t* Ri, int32_t n, int64_t* re_out, int64_t* im_out,
                        int32_t* e_out);

@@ -4,13 +4,14 @@
 // B300 executes FP64 at about 1/74 of its FP32 rate, while 32-bit integer
 // multiplies and adds issue at 1/2 to 1/1 of it.  This walk therefore keeps
 // everything in integers:
-//  - row i is scaled by 2^sigma_i (sum_j |a_ij| 2^sigma_i < 2^63; complex:
-//    the sum of |Re| + |Im|) and rounded to even int64 entries A_ij (each
-//    entry moves by at most 2^-62 sum_j |a_ij|), so every Gray-walk row sum
-//    R_i = X_i + sum_{j in S} A_ij of the rounded matrix is exact (no drift)
-//    and |R_i| < 2^62 + n (complex: |Re R_i| + |Im R_i| < 2^62 + 2n);
+//  - row i is scaled by 2^sigma_i (S 2^sigma_i in [2^62, 2^63) for the
+//    float64 sum S of |a_ij|; complex: of |Re| + |Im|) and rounded to even
+//    int64 entries A_ij (each entry moves by at most 2^-62 sum_j |a_ij|), so
+//    every Gray-walk row sum R_i = X_i + sum_{j in S} A_ij of the rounded
+//    matrix is exact (no drift) and |R_i| < 2^62 + 2^17 (complex: |Re R_i| +
+//    |Im R_i|; S may undercount the exact sum by up to 64 ulps);
 //  - a product of row sums is a float with a signed mantissa m (|m| in
-//    [2^61, 2^62 + 2^10]; complex: |Re m| + |Im m| <= 2^62 + 2^10) and an int
+//    [2^61, 2^62 + 2^20]; complex: |Re m| + |Im m| <= 2^62 + 2^20) and an int
 //    exponent.  A chain factor is m R >> 64, a combining factor m m' >> 62,
 //    each one truncated 64x64 -> 128-bit product from three signed
 //    32x32 -> 64-bit multiplies, then a leading-zero normalisation (a chain's

@@ -66,7 +66,7 @@ __host__ __device__ __forceinline__ XLimbs x64_limbs(int64_t a) {
     return XLimbs{(int32_t)x64_hiword(a) + (int32_t)(al >> 31), (int32_t)al};
 }
 
-// (a * b) >> 62 for |a|, |b| <= 2^62 + 2^10 (the result fits; every partial
+// (a * b) >> 62 for |a|, |b| <= 2^62 + 2^20 (the result fits; every partial
 // product keeps a margin of 2^31), truncated: the result is within [-2, +1]
 // of floor(a*b / 2^62).  The low product a0*b0 (< 2^62 in size) is dropped;
 // the rest is 4 (a1 b1 + floor(mid / 2^32)) + bits 30..31 of mid, with
@@ -78,10 +78,10 @@ __host__ __device__ __forceinline__ int64_t x64_mulhi62(int64_t a, int64_t b) {
     return (int64_t)(((uint64_t)r << 2) | (((uint64_t)mid >> 30) & 3u));
 }
 
-// (a * b) >> 64 for |a| <= 2^62 + 2^10, |b| < 2^63 - 2^32, truncated (within
+// (a * b) >> 64 for |a| <= 2^62 + 2^20, |b| < 2^63 - 2^32, truncated (within
 // [-2, +1] of the floor): a1 b1 + floor(mid / 2^32).  The walks use it for the
 // chain factors, whose row sums are staged two bits larger for it
-// (|R| < 2^62 + n).
+// (|R| < 2^62 + 2^17).
 __host__ __device__ __forceinline__ int64_t x64_mulhi64(int64_t a, int64_t b) {
     const XLimbs x = x64_limbs(a), y = x64_limbs(b);
     const int64_t mid = x64_madw(x.lo, y.hi, x64_mulw(x.hi, y.lo));
@@ -90,7 +90,7 @@ __host__ __device__ __forceinline__ int64_t x64_mulhi64(int64_t a, int64_t b) {
 
 // Complex product (ar + i ai)(br + i bi) >> SH by components (SH = 64: chain
 // factor, b a staged row sum; SH = 62: combining factor, b a mantissa), for
-// |ar| + |ai| <= 2^62 + 2^10 and |br| + |bi| <= 2^62 + 2^10: three products
+// |ar| + |ai| <= 2^62 + 2^20 and |br| + |bi| <= 2^62 + 2^20: three products
 // (Karatsuba), re = k1 - k3, im = k1 + k2, each k within [-2, +1] of its
 // floor, so each component is within 4 of the exact (ar br - ai bi) 2^-SH
 // (resp. (ar bi + ai br) 2^-SH).  A schoolbook form on twelve chained
@@ -168,7 +168,7 @@ __host__ __device__ __forceinline__ int64_t x64_scaled_round(double a, int k) {
 struct XReal { int64_t m; int e; };
 struct XCplx { int64_t re, im; int e; };
 
-// real: mantissa target |m| in [2^61, 2^62] (up to 2^62 + 2^10 where a staged
+// real: mantissa target |m| in [2^61, 2^62] (up to 2^62 + 2^20 where a staged
 // row sum or a product of such enters un-normalised: the shift is never negative)
 // Position of the most significant non-sign bit of the high word (-1 when the
 // word is 0 or -1): bfind.s32 on the GPU, the same value from the folded
@@ -195,7 +195,7 @@ __host__ __device__ __forceinline__ XReal x64_from_int(int64_t r) {
     const int s = x64_norm_shift_top<62>(x64_top_hi(r));
     return XReal{x64_shl(r, s), -s};
 }
-// The head of a product chain: a staged row sum (|R| < 2^62 + n) is already a
+// The head of a product chain: a staged row sum (|R| < 2^62 + 2^17) is already a
 // valid chain-factor operand, so it enters as it is (exponent 0) when a chain
 // factor follows (norm = false): that factor then truncates on the row sum's
 // own grid, as if the head were 2^62 in size, which the error bound counts.
@@ -216,7 +216,7 @@ __host__ __device__ __forceinline__ XReal x64_mul_row(XReal a, int64_t R) {
 }
 
 // complex: larger component target in [2^60, 2^61]; the invariant the products
-// need is |re| + |im| <= 2^62 + 2^10, which every product keeps
+// need is |re| + |im| <= 2^62 + 2^20, which every product keeps
 __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) {
     const int t1 = x64_top_hi(re), t2 = x64_top_hi(im);
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
@@ -225,7 +225,7 @@ __host__ __device__ __forceinline__ XCplx x64c_from_int(int64_t re, int64_t im) 
 __host__ __device__ __forceinline__ XCplx x64c_head(int64_t re, int64_t im, bool norm) {
     return norm ? x64c_from_int(re, im) : XCplx{re, im, 0};
 }
-// (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^10: the combining factor
+// (a.re + i a.im) * (br + i bi) * 2^-62, |br| + |bi| <= 2^62 + 2^20: the combining factor
 __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t bi, int eb) {
     int64_t re, im;
     x64c_mulhi<62>(a.re, a.im, br, bi, re, im);
@@ -233,7 +233,7 @@ __host__ __device__ __forceinline__ XCplx x64c_mul(XCplx a, int64_t br, int64_t 
     const int s = x64_norm_shift_top<61>(t1 > t2 ? t1 : t2);
     return XCplx{x64_shl(re, s), x64_shl(im, s), a.e + eb + 62 - s};
 }
-// a times a staged complex row sum (|br| + |bi| < 2^62 + 2n): the chain factor
+// a times a staged complex row sum (|br| + |bi| < 2^62 + 2^17): the chain factor
 __host__ __device__ __forceinline__ XCplx x64c_mul_row(XCplx a, int64_t br, int64_t bi) {
     int64_t re, im;
     x64c_mulhi<64>(a.re, a.im, br, bi, re, im);
@@ -309,7 +309,7 @@ __host__ __device__ __forceinline__ void x64_acc_add(XAcc& a, int64_t m, int e, 
 // a <- a + b, both aligned to the larger exponent (the smaller-exponent one
 // is shifted right).  The operation is symmetric in a and b, so a fixed
 // butterfly of merges gives the same bits on every lane and in every batch.
-// A term is below 2^103 on its accumulator's grid (|mantissa| <= 2^62 + 2^10,
+// A term is below 2^103 on its accumulator's grid (|mantissa| <= 2^62 + 2^20,
 // shift <= 40), a chunk of at most 2^16 terms below 2^119, and 32 merges keep
 // the sum below 2^124.
 __host__ __device__ __forceinline__ __int128 x64_sar128(__int128 v, int d) {

@@ -126,6 +126,33 @@ def test_mixed_requests_equal_batched_path(px, plain):
         S.close()
 
 
+def test_fp64_mode_server_equals_batched_path(px):
+    """A server created in FP64 mode keeps the double-double partial slots and
+    finalisation; its results equal the FP64-mode batched path bit for bit and
+    the oracle within the tolerance."""
+    old = px.permx_set_fp_arith(px.FP_ARITH_FP64)
+    S = None
+    try:
+        S = Server(px)
+        reqs = [r for r in _mix(11, 24) if r[1] != 2]
+        tickets = []
+        for A, f, p in reqs:
+            rc, t = S.submit(A, f, p)
+            assert rc == 0, px.last_error()
+            tickets.append((t, f))
+        res = S.wait(tickets)
+        for (A, f, p), (t, _) in zip(reqs, tickets):
+            v = res[t][0]
+            assert v == _batched(px, A, f, p), (A.shape[0], f)
+        for (A, f, p), (t, _) in list(zip(reqs, tickets))[:4]:
+            ref = O.perm_dp(A)
+            assert abs(res[t][0] - ref) <= 1e-9 * max(abs(ref), 1e-12), (A.shape[0], f)
+    finally:
+        if S is not None:
+            S.close()
+        px.permx_set_fp_arith(old)
+
+
 def test_arrivals_join_while_others_run(px):
     # a long request is admitted first; short ones submitted while it runs join at the
     # next step and finish before it (continuous batching, not a FIFO queue)

@@ -53,7 +53,7 @@ def _operands(rnd, count, amax, bmax):
 
 def test_combining_and_chain_products_match_host_and_bound(lib):
     rnd = random.Random(5)
-    lim = 2 ** 62 + 2 ** 10                     # combining operands: both mantissas
+    lim = 2 ** 62 + 2 ** 20                     # combining operands: both mantissas
     a, b = _operands(rnd, 40000, lim, lim)
     h62, h64 = _device(lib, a, b)
     for i, (x, y) in enumerate(zip(a, b)):
@@ -67,7 +67,7 @@ def test_chain_product_full_row_sum_range(lib):
     """Chain factors: the second operand is a staged row sum or a Karatsuba
     sum / difference of two row-sum components (|b| < 2^63 - 2^32)."""
     rnd = random.Random(6)
-    a, b = _operands(rnd, 40000, 2 ** 62 + 2 ** 10, 2 ** 63 - 2 ** 32 - 1)
+    a, b = _operands(rnd, 40000, 2 ** 62 + 2 ** 20, 2 ** 63 - 2 ** 32 - 1)
     _, h64 = _device(lib, a, b)
     for i, (x, y) in enumerate(zip(a, b)):
         assert h64[i] == lib.permx_x64_mulhi64(x, y), (x, y)
@@ -88,7 +88,7 @@ def test_complex_products_match_host_and_bound(lib):
     """Chain (>> 64) and combining (>> 62) complex factors on the GPU equal the
     host's bit for bit and stay within their truncation bounds."""
     rnd = random.Random(7)
-    top = 2 ** 62 + 2 ** 10
+    top = 2 ** 62 + 2 ** 20
 
     def operand():
         mag = rnd.choice((top, rnd.randint(0, top), rnd.randint(0, top) >> rnd.randint(0, 60)))

@@ -38,11 +38,14 @@ def _arr(v, t=np.int64):
 
 
 def test_mulhi62_truncation_bound(lib):
+    """Combining operands: mantissas up to 2^62 + 2^20 in size."""
     rnd = random.Random(1)
-    edge = [0, 1, -1, 2 ** 62, -2 ** 62, 2 ** 61, -(2 ** 61), 2 ** 62 - 1, -(2 ** 62) + 1, 2 ** 31, -(2 ** 31), 12345]
+    top = 2 ** 62 + 2 ** 20
+    edge = [0, 1, -1, top, -top, 2 ** 62, -2 ** 62, 2 ** 61, -(2 ** 61), 2 ** 62 - 1, -(2 ** 62) + 1, 2 ** 31,
+            -(2 ** 31), 12345]
     cases = [(a, b) for a in edge for b in edge]
-    cases += [(rnd.randint(-2 ** 62, 2 ** 62), rnd.randint(-2 ** 62, 2 ** 62)) for _ in range(20000)]
-    cases += [(rnd.randint(-2 ** 62, 2 ** 62), rnd.randint(-2 ** 40, 2 ** 40)) for _ in range(5000)]
+    cases += [(rnd.randint(-top, top), rnd.randint(-top, top)) for _ in range(20000)]
+    cases += [(rnd.randint(-top, top), rnd.randint(-2 ** 40, 2 ** 40)) for _ in range(5000)]
     for a, b in cases:
         got = lib.permx_x64_mulhi62(a, b)
         exact = (a * b) >> 62            # floor
@@ -51,8 +54,8 @@ def test_mulhi62_truncation_bound(lib):
 
 def test_mulhi64_truncation_bound(lib):
     """The chain factor's product: |a| <= 2^62 + 2^32 (a mantissa, or an
-    un-normalised first row sum), |b| < 2^63 - 2^32 (a row sum, or the Karatsuba
-    sum/difference of two row-sum components)."""
+    un-normalised first row sum; the stated bound is 2^62 + 2^20), |b| < 2^63 - 2^32
+    (a row sum, or the Karatsuba sum/difference of two row-sum components)."""
     rnd = random.Random(2)
     amax, bmax = 2 ** 62 + 2 ** 32, 2 ** 63 - 2 ** 32 - 1
     edge_a = [0, 1, -1, amax, -amax, 2 ** 62, -(2 ** 62), 2 ** 61, -(2 ** 61), 2 ** 31, -(2 ** 31), 2 ** 31 - 1]
@@ -78,7 +81,7 @@ def test_complex_mulhi_components_bound(lib):
     each component within 4 of the exact value's floor (Karatsuba: three
     truncated products, each within [-2, +1] of its floor)."""
     rnd = random.Random(3)
-    top = 2 ** 62 + 2 ** 10
+    top = 2 ** 62 + 2 ** 20
     re, im = ctypes.c_int64(), ctypes.c_int64()
     edges = [(top, 0), (-top, 0), (0, top), (0, -top), (top // 2, -(top - top // 2)), (2 ** 31, -(2 ** 31)), (0, 0)]
     cases = [(a, b) for a in edges for b in edges]
@@ -119,8 +122,9 @@ def _error_scale(R):
 def test_real_product(lib, n):
     rnd = random.Random(n)
     for trial in range(300):
-        # staged row sums: |R| < 2^62 + n (row scale 2^sigma with sum_j |a_ij| 2^sigma < 2^63)
-        top = 2 ** 62 + n
+        # staged row sums: |R| < 2^62 + 2^17 (row scale 2^sigma with the float64 row sum
+        # times 2^sigma below 2^63, which may undercount the exact sum by 64 ulps)
+        top = 2 ** 62 + 2 ** 17
         if trial % 10 == 0:
             R = [rnd.randint(-top, top) >> rnd.randint(0, 40) for _ in range(n)]
         elif trial % 10 == 1:
@@ -139,20 +143,20 @@ def test_real_product(lib, n):
         assert abs(got - exact) <= Fraction(4 * n, 2 ** 59) * _error_scale(R) + 0, (R, m.value, e.value)
         if exact == 0:
             assert m.value == 0
-        # mantissas: |m| <= 2^62 + 2^10 (a chain that is a lone staged row sum enters the
-        # combining products un-normalised, up to 2^62 + n; the overflow margin is 2^31)
+        # mantissas: |m| <= 2^62 + 2^20 (a chain that is a lone staged row sum enters the
+        # combining products un-normalised, up to 2^62 + 2^17)
         elif min(abs(r) for r in R) >= 2 ** 40:
-            assert 2 ** 61 <= abs(m.value) <= 2 ** 62 + 2 ** 10
+            assert 2 ** 61 <= abs(m.value) <= 2 ** 62 + 2 ** 20
         else:                      # tiny row sums may leave the mantissa partly normalised
-            assert abs(m.value) <= 2 ** 62 + 2 ** 10
+            assert abs(m.value) <= 2 ** 62 + 2 ** 20
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 11, 26])
 def test_complex_product(lib, n):
     rnd = random.Random(100 + n)
     for trial in range(200):
-        # staged complex row sums: |Re R| + |Im R| < 2^62 + 64
-        top = 2 ** 62 + 64
+        # staged complex row sums: |Re R| + |Im R| < 2^62 + 2^17
+        top = 2 ** 62 + 2 ** 17
         Rr, Ri = [], []
         for _ in range(n):
             mag = top if trial % 5 == 1 else rnd.randint(0, top)
@@ -175,7 +179,7 @@ def test_complex_product(lib, n):
         bound = Fraction(16 * n, 2 ** 59) * _error_scale(mags)
         assert abs(Fraction(re.value) * scale - er) <= bound
         assert abs(Fraction(im.value) * scale - ei) <= bound
-        assert abs(re.value) + abs(im.value) <= 2 ** 62 + 2 ** 10
+        assert abs(re.value) + abs(im.value) <= 2 ** 62 + 2 ** 20
 
 
 def test_accumulator_exact_sum(lib):
