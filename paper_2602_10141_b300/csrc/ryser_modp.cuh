@@ -92,6 +92,38 @@ __device__ __forceinline__ mont_t prod_tree(const uint32_t (&r)[N], uint32_t p, 
     return v[0];
 }
 
+// Two product trees formed level by level together (the paired steps' r and
+// r2): each level's products of both trees are independent, so the compiler
+// sees them side by side.  Same products, same order per tree as prod_tree.
+template <int N>
+__device__ __forceinline__ void prod_tree2(const uint32_t (&r)[N], const uint32_t (&r2)[N], uint32_t p,
+                                           uint32_t pinv, int32_t z, mont_t& out1, mont_t& out2) {
+    mont_t v[N], w[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        v[i] = (mont_t)r[i];
+        w[i] = (mont_t)r2[i];
+    }
+#pragma unroll
+    for (int lvl = 0; lvl < 6; ++lvl) {
+        const int n_live = (N + (1 << lvl) - 1) >> lvl;
+        if (n_live > 1) {
+#pragma unroll
+            for (int i = 0; i < N / 2; ++i)
+                if (i < n_live / 2) {
+                    v[i] = mont_mul(v[2 * i], v[2 * i + 1], p, pinv, z);
+                    w[i] = mont_mul(w[2 * i], w[2 * i + 1], p, pinv, z);
+                }
+            if (n_live & 1) {
+                v[n_live / 2] = v[n_live - 1];
+                w[n_live / 2] = w[n_live - 1];
+            }
+        }
+    }
+    out1 = v[0];
+    out2 = w[0];
+}
+
 // dst_i = src_i +- (column j)_i mod p
 template <int N, bool SUB>
 __device__ __forceinline__ void column_step(uint32_t (&dst)[N], const uint32_t (&src)[N],
@@ -214,8 +246,8 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                 uint32_t r2[N];
                 if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
                 else column_step<N, false>(r2, r, col, p, z0);
-                const mont_t te = prod_tree<N>(r, p, pinv, (int32_t)z0);
-                const mont_t to = prod_tree<N>(r2, p, pinv, (int32_t)z0);
+                mont_t te, to;
+                prod_tree2<N>(r, r2, p, pinv, (int32_t)z0, te, to);
                 E += pe;
                 O += po;
                 pe = te;
