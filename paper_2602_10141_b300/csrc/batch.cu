@@ -19,6 +19,7 @@
 #include "batch.h"
 #include "common.cuh"
 #include "finalize.cuh"
+#include "pdl.cuh"
 #include "x64_arith.cuh"
 
 namespace permx {
@@ -132,9 +133,14 @@ int sm_count() {
 // row (the float sum in column order), the conversions one thread per entry,
 // in integer operations.
 constexpr int kStageX64Threads = 128;
-template <int W>
+struct NoWork {
+    __device__ void operator()() const {}
+};
+// mid() runs while the matrix loads are in flight (the set-up kernel's
+// metadata copy), before the first barrier.
+template <int W, typename Mid = NoWork>
 __device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, const StageDesc s,
-                                                int64_t* __restrict__ colT) {
+                                                int64_t* __restrict__ colT, Mid mid = Mid()) {
     // the matrix, row-major: the float entries, each replaced in place by its
     // integer A_ij once the row scales are known
     __shared__ long long buf[PERMX_MAX_N_FP * PERMX_MAX_N_FP * W];
@@ -149,11 +155,26 @@ __device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, co
         sig_sum = 0;
         bad = 0;
     }
+    mid();
     __syncthreads();
-    // the row scale from sum_j |a_ij|, summed in column order by one thread per row
+    // the row scale from sum_j |a_ij|, one thread per row: four interleaved
+    // partial sums over the row's words (words 0, 4, 8, ... in s0), then
+    // (s0 + s1) + (s2 + s3); FP64 latency on B300 is ~64 cycles per dependent
+    // add, so a single running sum would dominate the staging
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double S = 0.0;
-        for (int j = 0; j < nw; ++j) S += fabs(__longlong_as_double(buf[i * nw + j]));
+        const long long* row = buf + i * nw;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
+        for (; j + 4 <= nw; j += 4) {
+            s0 += fabs(__longlong_as_double(row[j]));
+            s1 += fabs(__longlong_as_double(row[j + 1]));
+            s2 += fabs(__longlong_as_double(row[j + 2]));
+            s3 += fabs(__longlong_as_double(row[j + 3]));
+        }
+        if (j < nw) s0 += fabs(__longlong_as_double(row[j]));
+        if (j + 1 < nw) s1 += fabs(__longlong_as_double(row[j + 1]));
+        if (j + 2 < nw) s2 += fabs(__longlong_as_double(row[j + 2]));
+        const double S = (s0 + s1) + (s2 + s3);
         // a NaN or infinite entry makes S non-finite: the matrix is flagged (its
         // permanent is reported as NaN) and the row staged as zeros
         const bool finite = isfinite(S);
@@ -181,8 +202,19 @@ __device__ __forceinline__ void stage_x64_block(const double* __restrict__ A, co
     // exact (entries are even), summed in halves so no partial sum leaves int64
     for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
         const int i = e / W, w = e - i * W;
-        int64_t half = 0;
-        for (int j = 0; j < n - 1; ++j) half += buf[i * nw + j * W + w] / 2;
+        const long long* col0 = buf + i * nw + w;
+        int64_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // exact integer sums: the split changes no bit
+        int j = 0;
+        for (; j + 4 <= n - 1; j += 4) {
+            h0 += col0[j * W] / 2;
+            h1 += col0[(j + 1) * W] / 2;
+            h2 += col0[(j + 2) * W] / 2;
+            h3 += col0[(j + 3) * W] / 2;
+        }
+        if (j < n - 1) h0 += col0[j * W] / 2;
+        if (j + 1 < n - 1) h1 += col0[(j + 1) * W] / 2;
+        if (j + 2 < n - 1) h2 += col0[(j + 2) * W] / 2;
+        const int64_t half = (h0 + h1) + (h2 + h3);
         base[((int64_t)n * ld + i) * W + w] = buf[i * nw + (n - 1) * W + w] / 2 - half;
     }
     if (threadIdx.x == 0) {
@@ -195,6 +227,7 @@ template <int W>
 __global__ void __launch_bounds__(kStageX64Threads) stage_x64_kernel(const double* __restrict__ A,
                                                                    const StageDesc* __restrict__ d,
                                                                    int64_t* __restrict__ colT) {
+    grid_dep_allow();
     stage_x64_block<W>(A, d[blockIdx.x], colT);
 }
 
@@ -252,6 +285,7 @@ __device__ __forceinline__ void stage_columns_block(const T* __restrict__ A, con
 
 template <typename T>
 __global__ void stage_columns_kernel(const T* __restrict__ A, const StageDesc* __restrict__ d, T* __restrict__ colT) {
+    grid_dep_allow();
     stage_columns_block<T>(A, d[blockIdx.x], colT);
 }
 
@@ -277,6 +311,7 @@ template <int SZ, typename T>
 __global__ void setup_columns_kernel(const T* __restrict__ A, const __grid_constant__ MetaBytes<SZ> m,
                                      uint32_t* __restrict__ ws, uint32_t zero_from, uint32_t zero_words,
                                      T* __restrict__ colT) {
+    grid_dep_allow();   // the walk may be scheduled now; it waits for this kernel (pdl.cuh)
     setup_meta(m, ws, zero_from, zero_words);
     stage_columns_block<T>(A, reinterpret_cast<const StageDesc*>(m.w)[blockIdx.x], colT);
 }
@@ -285,8 +320,9 @@ __global__ void __launch_bounds__(kStageX64Threads) setup_x64_kernel(const doubl
                                                                    const __grid_constant__ MetaBytes<SZ> m,
                                                                    uint32_t* __restrict__ ws, uint32_t zero_from,
                                                                    uint32_t zero_words, int64_t* __restrict__ colT) {
-    setup_meta(m, ws, zero_from, zero_words);
-    stage_x64_block<W>(A, reinterpret_cast<const StageDesc*>(m.w)[blockIdx.x], colT);
+    grid_dep_allow();   // the walk may be scheduled now; it waits for this kernel (pdl.cuh)
+    stage_x64_block<W>(A, reinterpret_cast<const StageDesc*>(m.w)[blockIdx.x], colT,
+                       [&] { setup_meta(m, ws, zero_from, zero_words); });
 }
 
 __global__ void finalize_modp_kernel(const unsigned long long* __restrict__ acc, const ModpFinal* __restrict__ f,

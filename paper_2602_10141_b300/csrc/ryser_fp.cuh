@@ -13,6 +13,7 @@
 #pragma once
 #include "common.cuh"
 #include "finalize.cuh"
+#include "pdl.cuh"
 
 namespace permx {
 
@@ -89,6 +90,7 @@ __device__ __forceinline__ void decode_fp_item(const FpLaunch& L, uint64_t item,
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, 1) ryser_f64_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     constexpr int NP = pad2(N);
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_f64_kernel(const FpLau
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, 1) ryser_c128_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
@@ -214,13 +217,11 @@ __global__ void __launch_bounds__(kRyserThreads, 1) ryser_c128_kernel(const FpLa
 
 template <int N>
 cudaError_t launch_f64(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
-    ryser_f64_kernel<N><<<grid, threads, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_dependent(ryser_f64_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 template <int N>
 cudaError_t launch_c128(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
-    ryser_c128_kernel<N><<<grid, threads, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_dependent(ryser_c128_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 template <int N>
 int blocks_per_sm_f64() {

@@ -21,6 +21,7 @@
 #pragma once
 #include "common.cuh"
 #include "finalize.cuh"
+#include "pdl.cuh"
 
 namespace permx {
 
@@ -177,6 +178,7 @@ __device__ __forceinline__ void toggle_column(uint32_t (&r)[N], const uint32_t* 
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_kernel(const ModpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     constexpr int NP = pad4(N);
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -281,8 +283,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
 
 template <int N>
 cudaError_t launch_modp(const ModpLaunch& L, int grid, int threads, cudaStream_t s) {
-    ryser_modp_kernel<N><<<grid, threads, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_dependent(ryser_modp_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 
 template <int N>

@@ -67,6 +67,7 @@ template <int N> constexpr int x64c_minb() { return N <= 16 ? 2 : 1; }   // 3 bl
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     constexpr int NP = pad2(N);
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
 
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t chunk_mask = (1ull << L.log2_chunks) - 1;
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
 // so lane groups are min(chunks, 16) chunks wide.
 template <int N>
 __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     constexpr int H = (N + 1) / 2;
     const int lane = threadIdx.x & 31;
     const int h = lane & 1;
@@ -387,6 +390,7 @@ __device__ __forceinline__ XCplx shfl_cplx(unsigned mask, const XCplx& t, int sr
 
 template <int N>
 __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunch L) {
+    grid_dep_wait();   // the set-up kernel before it has completed (pdl.cuh)
     static_assert(N >= 8 && N <= 16, "the four-lane walk covers 8 <= n <= 16");
     constexpr int RQ = (N + 3) / 4;                 // rows of lane 0 (lanes with q >= N % 4 may own one fewer)
     __shared__ long long sh[4][2][4];               // per warp: (re, im) accumulators for the cross-warp levels
@@ -523,8 +527,7 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
 
 template <int N>
 cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
-    ryser_x64r_kernel<N><<<grid, threads, 0, s>>>(L);
-    return cudaGetLastError();
+    return launch_dependent(ryser_x64r_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 template <int N>
 cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
@@ -532,13 +535,11 @@ cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s
         // fewer one-lane warps than SM sub-partitions: four lanes per chunk (same bits)
         const uint64_t items = L.item_end - L.item_begin;
         if (items < (uint64_t)sm_count() * 128) {
-            ryser_x64c4_kernel<N><<<(unsigned)((items + 31) / 32), kQuadThreads, 0, s>>>(L);
-            return cudaGetLastError();
+            return launch_dependent(ryser_x64c4_kernel<N>, (unsigned)((items + 31) / 32), (unsigned)kQuadThreads, s, L);
         }
     }
-    if constexpr (x64c_paired(N)) ryser_x64c2_kernel<N><<<grid, threads, 0, s>>>(L);
-    else ryser_x64c_kernel<N><<<grid, threads, 0, s>>>(L);
-    return cudaGetLastError();
+    if constexpr (x64c_paired(N)) return launch_dependent(ryser_x64c2_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
+    else return launch_dependent(ryser_x64c_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 template <int N>
 int blocks_per_sm_x64r() {
