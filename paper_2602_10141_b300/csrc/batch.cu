@@ -125,13 +125,13 @@ int sm_count() {
 // ---------------------------------------------------------------------------
 
 // Integer-mantissa staging of one matrix by one block: row i gets the scale
-// sigma_i = 60 - floor(log2(sum_j |a_ij|)) (complex: |re| + |im|), entries
+// sigma_i = 62 - floor(log2(sum_j |a_ij|)) (complex: |re| + |im|), entries
 // A_ij = 2 round(a_ij 2^(sigma_i - 1)) (even, so halves are exact), the
-// Nijenhuis-Wilf column X_i = A_{i,n-1} - (sum_j A_ij)/2, zero padding, and
-// one trailing word with -sum_i sigma_i.  W = int64 words per entry.  The
+// Nijenhuis-Wilf column X_i = A_{i,n-1}/2 - sum_{j<n-1} A_ij/2, zero padding,
+// and one trailing word with -sum_i sigma_i.  W = int64 words per entry.  The
 // matrix is read once into shared memory; the row scales take one thread per
-// row (the float sum in column order), the conversions one thread per entry,
-// in integer operations.
+// row (the float sum as four interleaved partial sums), the conversions one
+// thread per entry, in integer operations.
 constexpr int kStageX64Threads = 128;
 struct NoWork {
     __device__ void operator()() const {}
