@@ -478,7 +478,7 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
     for cplx, field in fields_keys.items():
         for n in SIZES:
             if tune:
-                table[f"{'c128' if cplx else 'f64'}:{n}"] = px.perm_autotune(field, n, _tune_batch(n), 3)
+                table[f"{'c128' if cplx else 'f64'}:{n}"] = px.perm_autotune(field, n, _tune_batch(n), 5)
             else:
                 table[f"{'c128' if cplx else 'f64'}:{n}"] = px.perm_tune_get(field, n)
     tune_s = time.perf_counter() - t0

@@ -239,7 +239,8 @@ int perm_graph_destroy(perm_graph* graph);
  * 128-bit chunk accumulator needs the headroom; EINVAL otherwise); perm_tune_get
  * returns the ell in force; perm_autotune times ell0-3 .. ell0+3 around the
  * built-in rule on a synthetic batch of `batch` n x n matrices (`reps`
- * timed passes each), keeps the fastest in the table and returns it. */
+ * passes each, each timed on its own; a candidate counts by its fastest pass),
+ * keeps the fastest candidate in the table and returns it. */
 #define PERMX_MAX_ELL_FP 16
 #define PERMX_MAX_ELL_MODP 30
 int perm_tune_set(int field, int32_t n, int32_t ell);

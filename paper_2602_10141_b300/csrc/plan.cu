@@ -368,14 +368,20 @@ int perm_autotune(int field, int32_t n, int64_t batch, int32_t reps, int32_t* be
         rc = prepare_batch((Field)field, nn.data(), off.data(), pp.data(), batch, s, X);
         if (rc) break;
         rc = execute_batch(X, A, out, s);   // warm-up
-        cudaEventRecord(e0, s);
-        for (int r = 0; rc == PERMX_OK && r < reps; ++r) rc = execute_batch(X, A, out, s);
-        cudaEventRecord(e1, s);
-        e = cudaEventSynchronize(e1);
+        // each repetition timed on its own; the candidate's time is the fastest
+        // one (interference from other work only ever adds time)
+        float ms = 1e30f;
+        for (int r = 0; rc == PERMX_OK && r < reps; ++r) {
+            cudaEventRecord(e0, s);
+            rc = execute_batch(X, A, out, s);
+            cudaEventRecord(e1, s);
+            e = cudaEventSynchronize(e1);
+            if (rc == PERMX_OK && e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+            float t = 0.f;
+            if (rc == PERMX_OK) cudaEventElapsedTime(&t, e0, e1);
+            if (rc == PERMX_OK && t < ms) ms = t;
+        }
         release_batch(X, s);
-        if (rc == PERMX_OK && e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
         if (rc == PERMX_OK && ms < best_ms) {
             best_ms = ms;
             best = ell;
