@@ -47,9 +47,9 @@ void tune_set(int field, int n, int ell) {
 
 int chunk_log2(Field field, int n, int bits) {
     const int t = tune_get((int)field, n);
-    if (t > 0 && t <= bits) return t;
-    if (t > bits) return bits;
-    return field == Field::MODP ? chunk_log2_modp(bits) : chunk_log2_fp(bits);
+    int ell = t > 0 ? (t < bits ? t : bits) : (field == Field::MODP ? chunk_log2_modp(bits) : chunk_log2_fp(bits));
+    if (field == Field::MODP && ell > kModpMaxEll) ell = kModpMaxEll;   // the walk counts steps in 32 bits
+    return ell;
 }
 
 int chunk_log2_fp(int bits) {

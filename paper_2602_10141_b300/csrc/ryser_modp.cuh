@@ -166,10 +166,10 @@ __device__ __forceinline__ void apply_column(uint32_t (&r)[N], const uint32_t* _
 // Step into Gray index k (k >= 1): column j = ctz(k) enters the subset if bit
 // j+1 of k is clear, leaves it otherwise.
 template <int N>
-__device__ __forceinline__ void toggle_column(uint32_t (&r)[N], const uint32_t* __restrict__ col, uint64_t k,
+__device__ __forceinline__ void toggle_column(uint32_t (&r)[N], const uint32_t* __restrict__ col, uint32_t k,
                                               uint32_t p) {
     constexpr int NP = pad4(N);
-    const int j = __ffsll((long long)k) - 1;
+    const int j = __ffs((int)k) - 1;
     if ((k >> (j + 1)) & 1) apply_column<N, true>(r, col + j * NP, p);
     else apply_column<N, false>(r, col + j * NP, p);
 }
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             }
         }
         uint32_t part = 0;
-        uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+        const uint64_t k0 = c << L.ell;
+        uint64_t ks = k0, ke = k0 + (1ull << L.ell);
         ks = ks > L.k_lo ? ks : L.k_lo;
         ke = ke < L.k_hi ? ke : L.k_hi;
         if (valid && ks < ke) {
@@ -228,11 +229,16 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                 if ((S0 >> j) & 1) apply_column<N, false>(r, col + j * NP, p);
 
             term_acc_t E = 0, O = 0;
-            uint64_t k = ks;
+            // the walk counts k modulo 2^(ell+1) in 32 bits (ell <= 30): bit ell
+            // of k is bit 0 of the chunk index, and every step of the chunk
+            // reads bits 0..ell only (toggled column, its sign, the parity)
+            const uint32_t cb = (uint32_t)(c & 1) << L.ell;
+            uint32_t k = (uint32_t)(ks - k0) + cb;
+            const uint32_t ke32 = (uint32_t)(ke - k0) + cb;
             if (k & 1) {                       // a window may start on an odd index
                 O += prod_tree<N>(r, p, pinv, (int32_t)z0);
                 ++k;
-                if (k < ke) toggle_column<N>(r, col, k, p);
+                if (k < ke32) toggle_column<N>(r, col, k, p);
             }
             // pairs (k even, k+1): the step k -> k+1 toggles column 0; both
             // products are formed from independent arrays, which doubles the
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             // instruction of the pair waits for the trees' last levels and the
             // next pair's column steps and trees issue behind them.
             mont_t pe = 0, po = 0;
-            while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke) {
+            while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke32) {
                 uint32_t r2[N];
                 if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
                 else column_step<N, false>(r2, r, col, p, z0);
@@ -253,16 +259,16 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                 pe = te;
                 po = to;
                 k += 2;
-                if (k >= ke) break;          // the chunk is done; r is not needed again
-                const int j = __ffsll((long long)k) - 1;
+                if (k >= ke32) break;        // the chunk is done; r is not needed again
+                const int j = __ffs((int)k) - 1;
                 if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p, z0);
                 else column_step<N, false>(r, r2, col + j * NP, p, z0);
             }
             E += pe;
             O += po;
-            for (; k < ke; ++k) {              // remaining steps one at a time
+            for (; k < ke32; ++k) {            // remaining steps one at a time
                 if (k & 1) O += prod_tree<N>(r, p, pinv, (int32_t)z0); else E += prod_tree<N>(r, p, pinv, (int32_t)z0);
-                if (k + 1 < ke) toggle_column<N>(r, col, k + 1, p);
+                if (k + 1 < ke32) toggle_column<N>(r, col, k + 1, p);
             }
 #if PERMX_MODP_SIGNED
             long long d = (E - O) % (long long)p;       // |E - O| < 2^(ell+31) <= 2^63
@@ -281,6 +287,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
 
 template <int N>
 cudaError_t launch_modp(const ModpLaunch& L, int grid, int threads, cudaStream_t s) {
+    if (L.ell < 0 || L.ell > kModpMaxEll) return cudaErrorInvalidValue;   // 32-bit step counter
     return launch_dependent(ryser_modp_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 

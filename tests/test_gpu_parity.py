@@ -104,6 +104,26 @@ def test_modp_edge_values(px):
         assert int(v) == O.perm_modp_dp(A, p)
 
 
+@pytest.mark.parametrize("ell", [1, 2, 3])
+def test_modp_short_tuned_chunks(px, ell):
+    # chunks of 2^ell steps: most chunk indices are odd, and the last toggle of
+    # every chunk takes its sign from bit ell of k, i.e. from the chunk index
+    g = rng(1050 + ell)
+    primes = [2147483629, 65537, 2147483647, 1000003]
+    ns = [9, 13, 17, 20]
+    old = {n: px.perm_tune_get(px.FIELD_MODP, n) for n in ns}
+    try:
+        for n in ns:
+            px.perm_tune_set(px.FIELD_MODP, n, ell)
+        mats = [random_residues(n, primes[i], g) for i, n in enumerate(ns)]
+        got = run_modp(px, mats, primes)
+    finally:
+        for n in ns:
+            px.perm_tune_set(px.FIELD_MODP, n, old[n])
+    for A, p, v in zip(mats, primes, got):
+        assert int(v) == O.perm_modp_dp(A, p), (A.shape[0], p, ell)
+
+
 @pytest.mark.parametrize("n", [25, 26])
 def test_modp_larger_sizes(px, n):
     g = rng(1100 + n)
