@@ -45,9 +45,8 @@ WORKLOAD = "schur_n33_fp_5primes"
 # small case (bench.py --profile-case: 2^30 Gray steps of S_33 mod p, the same kernel), from
 # one ncu capture of the current build; not scaled to the bench launch (5 x 2^32 steps): the
 # walk reads its residue tables once and otherwise only instruction fetch reaches DRAM, which
-# grows far slower than the launch (0.96 MB measured once at full size); see
-# profiles/ryser_modp_n33_schur.md
-WALK_DRAM_BYTES_SMALL_CASE = 402_432
+# does not grow in proportion to the launch
+WALK_DRAM_BYTES_SMALL_CASE = 39_936
 
 
 def _rank_env():
