@@ -4,8 +4,8 @@
 // matrix.  At the chunk start it forms the row sums r_i = sum_{j in S} a_ij of
 // S = k ^ (k >> 1) from scratch; then every step k -> k+1 toggles column
 // j = ctz(k+1): r_i += a_ij if that bit of S turns on, r_i -= a_ij if it turns
-// off.  The term prod_i r_i enters with sign (-1)^{|S_k|} = (-1)^k, so even
-// and odd k are summed separately (E, O) and the chunk contributes E - O.
+// off.  The term prod_i r_i enters with sign (-1)^{|S_k|} = (-1)^k, and the
+// chunk contributes the signed sum D of its terms.
 //
 // Arithmetic: row sums are residues in [0, p), p < 2^31; modular add/sub use
 // one add and an unsigned min.  Products use signed Montgomery reduction with
@@ -17,7 +17,7 @@
 // product stays in (-p, p) with no correction step, and the next product
 // takes it as it is.  The product of n row sums by n-1 such steps carries
 // R^{-(n-1)}; the finalize step multiplies it back.  Terms are summed in
-// int64 without reduction (L * 2^31 < 2^63) and reduced once per chunk.
+// int64 without reduction (|D| < L 2^31 <= 2^61) and reduced once per chunk.
 #pragma once
 #include "common.cuh"
 #include "finalize.cuh"
@@ -48,7 +48,6 @@ __device__ __forceinline__ uint32_t mod_sub(uint32_t r, uint32_t a, uint32_t p, 
 
 #if PERMX_MODP_SIGNED
 typedef int32_t mont_t;       // product-tree values in (-p, p)
-typedef long long term_acc_t;
 // a * b * 2^-32 mod p for |a|, |b| < p, result in (-p, p)
 __device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, uint32_t p, uint32_t pinv, int32_t z) {
     const long long T = (long long)a * b;
@@ -58,7 +57,6 @@ __device__ __forceinline__ int32_t mont_mul(int32_t a, int32_t b, uint32_t p, ui
 }
 #else
 typedef uint32_t mont_t;      // product-tree values in [0, p)
-typedef unsigned long long term_acc_t;
 // (-p, p) -> [0, p): a negative value wraps above p, so the unsigned min picks r + p
 __device__ __forceinline__ uint32_t mont_fix(uint32_t r, uint32_t p) { return min(r, r + p); }
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv, int32_t z) {
@@ -228,7 +226,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             for (int j = 0; j < N; ++j)
                 if ((S0 >> j) & 1) apply_column<N, false>(r, col + j * NP, p);
 
-            term_acc_t E = 0, O = 0;
+            long long D = 0;                   // sum of (-1)^k prod_i r_i over the chunk
             // the walk counts k modulo 2^(ell+1) in 32 bits (ell <= 30): bit ell
             // of k is bit 0 of the chunk index, and every step of the chunk
             // reads bits 0..ell only (toggled column, its sign, the parity)
@@ -236,7 +234,7 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             uint32_t k = (uint32_t)(ks - k0) + cb;
             const uint32_t ke32 = (uint32_t)(ke - k0) + cb;
             if (k & 1) {                       // a window may start on an odd index
-                O += prod_tree<N>(r, p, pinv, (int32_t)z0);
+                D -= prod_tree<N>(r, p, pinv, (int32_t)z0);
                 ++k;
                 if (k < ke32) toggle_column<N>(r, col, k, p);
             }
@@ -244,39 +242,38 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             // products are formed from independent arrays, which doubles the
             // instruction-level parallelism of the product trees.  r2 is
             // computed from r and the next r from r2, so no array is copied.
-            // A pair's two products are added to E and O one pair later, so no
-            // instruction of the pair waits for the trees' last levels and the
-            // next pair's column steps and trees issue behind them.
+            // A pair's two products enter D one pair later, so no instruction
+            // of the pair waits for the trees' last levels and the next pair's
+            // column steps and trees issue behind them.  The loop tests once
+            // per pair: the step after the last pair is taken too and unused.
             mont_t pe = 0, po = 0;
-            while (N <= PERMX_MODP_PAIR_MAX_N && k + 1 < ke32) {
-                uint32_t r2[N];
-                if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
-                else column_step<N, false>(r2, r, col, p, z0);
-                mont_t te, to;
-                prod_tree2<N>(r, r2, p, pinv, (int32_t)z0, te, to);
-                E += pe;
-                O += po;
-                pe = te;
-                po = to;
-                k += 2;
-                if (k >= ke32) break;        // the chunk is done; r is not needed again
-                const int j = __ffs((int)k) - 1;
-                if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p, z0);
-                else column_step<N, false>(r, r2, col + j * NP, p, z0);
+            const uint32_t kp = ke32 - ((ke32 - k) & 1);   // pairs cover [k, kp)
+            if (N <= PERMX_MODP_PAIR_MAX_N && k < kp) {
+                do {
+                    uint32_t r2[N];
+                    if ((k >> 1) & 1) column_step<N, true>(r2, r, col, p, z0);
+                    else column_step<N, false>(r2, r, col, p, z0);
+                    mont_t te, to;
+                    prod_tree2<N>(r, r2, p, pinv, (int32_t)z0, te, to);
+                    D += (long long)pe - po;
+                    pe = te;
+                    po = to;
+                    k += 2;
+                    // the next step, also after the last pair (then unused; the
+                    // column index is clamped so the loads stay in the table)
+                    const int j = min(__ffs((int)k) - 1, min(N - 1, 30));
+                    if ((k >> (j + 1)) & 1) column_step<N, true>(r, r2, col + j * NP, p, z0);
+                    else column_step<N, false>(r, r2, col + j * NP, p, z0);
+                } while (k < kp);
             }
-            E += pe;
-            O += po;
+            D += (long long)pe - po;
             for (; k < ke32; ++k) {            // remaining steps one at a time
-                if (k & 1) O += prod_tree<N>(r, p, pinv, (int32_t)z0); else E += prod_tree<N>(r, p, pinv, (int32_t)z0);
+                const long long t = prod_tree<N>(r, p, pinv, (int32_t)z0);
+                D += (k & 1) ? -t : t;
                 if (k + 1 < ke32) toggle_column<N>(r, col, k + 1, p);
             }
-#if PERMX_MODP_SIGNED
-            long long d = (E - O) % (long long)p;       // |E - O| < 2^(ell+31) <= 2^63
+            const long long d = D % (long long)p;       // |D| < 2^(ell+31) <= 2^61
             part = (uint32_t)(d < 0 ? d + (long long)p : d);
-#else
-            const uint32_t e = (uint32_t)(E % p), o = (uint32_t)(O % p);
-            part = (e >= o) ? (e - o) : (e + p - o);
-#endif
         }
         // sum the group's partials mod p (all lanes of a group share m and p)
         for (int d = 1; d < G; d <<= 1) part = mod_add(part, __shfl_xor_sync(0xffffffffu, part, d), p);
