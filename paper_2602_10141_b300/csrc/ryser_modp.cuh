@@ -155,7 +155,11 @@ __device__ __forceinline__ void apply_column(uint32_t (&r)[N], const uint32_t* _
 }
 
 #ifndef PERMX_MODP_PAIR_MAX_N
-#define PERMX_MODP_PAIR_MAX_N 40   // pairwise steps while the two copies fit the register budget
+// Paired steps up to n = 46.  From n = 42 ptxas spills some of the second
+// row-sum copy at 128 registers, and the pairs still win: S_n Gray windows of
+// 2^36 steps gain 2-9 % at n = 41-46.  At n = 47, 48 the spills cost more than
+// the pairs gain; one block per SM with no spills was slower at every n > 40.
+#define PERMX_MODP_PAIR_MAX_N 46
 #endif
 #ifndef PERMX_MODP_MINB
 #define PERMX_MODP_MINB 2   // resident blocks of 256 threads per SM the register budget targets

@@ -394,6 +394,18 @@ def test_modp_n48_gray_window(px):
         assert px.perm_modp_gray_range(dA, 48, p, k0, k0 + 600000) == O.ryser_modp_gray_range(A, p, k0, k0 + 600000)
 
 
+@pytest.mark.parametrize("n", [41, 44, 46])
+def test_modp_paired_large_n_gray_window(px, n):
+    # n = 41..46 take the paired steps with a few registers spilled: sampled Gray
+    # windows (one starting on an odd index) against the oracle
+    g = rng(4300 + n)
+    p = 2147483629
+    A = random_residues(n, p, g)
+    dA = _dev(A.astype(np.int32))
+    for k0 in ((1 << (n - 1)) - 200000, (1 << (n - 2)) + 4321):
+        assert px.perm_modp_gray_range(dA, n, p, k0, k0 + 400000) == O.ryser_modp_gray_range(A, p, k0, k0 + 400000)
+
+
 def test_n1_all_fields(px, arith):
     assert run_fp(px, [np.array([[2.5 - 1j]])])[0] == 2.5 - 1j
     assert run_fp(px, [np.array([[-3.25]])])[0] == -3.25
