@@ -87,7 +87,10 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const int64_t* col = reinterpret_cast<const int64_t*>(cold);
-            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            const uint64_t ks = c << L.ell;
+            // the walk counts k modulo 2^(ell+1) in 32 bits: bit ell of k is
+            // bit 0 of the chunk index, and the steps read bits 0..ell only
+            const uint32_t kb = (uint32_t)(c & 1) << L.ell, kz = kb + (1u << L.ell);
             int64_t R[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) R[i] = col[N * NP + i];             // X_i
@@ -105,9 +108,9 @@ __global__ void __launch_bounds__(kRyserThreads, x64r_minb<N>()) ryser_x64r_kern
             }
             scale = (int)col[(N + 1) * NP];
             nonfinite = col[(N + 1) * NP + 1] != 0;
-            for (uint64_t k = ks; k < ke; ++k) {
-                if (k > ks) {
-                    const int j = __ffsll((long long)k) - 1;
+            for (uint32_t k = kb; k < kz; ++k) {
+                if (k > kb) {
+                    const int j = __ffs((int)k) - 1;
                     const longlong2* c2 = reinterpret_cast<const longlong2*>(col + j * NP);
                     if ((k >> (j + 1)) & 1) {
 #pragma unroll
@@ -163,7 +166,10 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const longlong2* col = reinterpret_cast<const longlong2*>(cold);
-            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            const uint64_t ks = c << L.ell;
+            // the walk counts k modulo 2^(ell+1) in 32 bits: bit ell of k is
+            // bit 0 of the chunk index, and the steps read bits 0..ell only
+            const uint32_t kb = (uint32_t)(c & 1) << L.ell, kz = kb + (1u << L.ell);
             int64_t Rr[N], Ri[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
@@ -184,9 +190,9 @@ __global__ void __launch_bounds__(kRyserThreads, x64c_minb<N>()) ryser_x64c_kern
             }
             scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
             nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
-            for (uint64_t k = ks; k < ke; ++k) {
-                if (k > ks) {
-                    const int j = __ffsll((long long)k) - 1;
+            for (uint32_t k = kb; k < kz; ++k) {
+                if (k > kb) {
+                    const int j = __ffs((int)k) - 1;
                     if ((k >> (j + 1)) & 1) {
 #pragma unroll
                         for (int i = 0; i < N; ++i) {
@@ -257,7 +263,10 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
         const unsigned pair_mask = __ballot_sync(0xffffffffu, valid);   // both lanes of a pair agree
         if (valid) {
             const longlong2* col = reinterpret_cast<const longlong2*>(cold);
-            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            const uint64_t ks = c << L.ell;
+            // the walk counts k modulo 2^(ell+1) in 32 bits: bit ell of k is
+            // bit 0 of the chunk index, and the steps read bits 0..ell only
+            const uint32_t kb = (uint32_t)(c & 1) << L.ell, kz = kb + (1u << L.ell);
             int64_t Rr[H], Ri[H];
 #pragma unroll
             for (int i = 0; i < H; ++i) {
@@ -284,9 +293,9 @@ __global__ void __launch_bounds__(kRyserThreads, 2) ryser_x64c2_kernel(const FpL
             }
             scale = (int)reinterpret_cast<const int64_t*>(col + (N + 1) * N)[0];
             nonfinite = reinterpret_cast<const int64_t*>(col + (N + 1) * N)[1] != 0;
-            for (uint64_t k = ks; k < ke; ++k) {
-                if (k > ks) {
-                    const int j = __ffsll((long long)k) - 1;
+            for (uint32_t k = kb; k < kz; ++k) {
+                if (k > kb) {
+                    const int j = __ffs((int)k) - 1;
                     const longlong2* cj = col + j * N + r0;
                     if ((k >> (j + 1)) & 1) {
 #pragma unroll
@@ -414,7 +423,10 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
         if (valid) decode_fp_item(L, item, chunk_mask, lg, valid, cold, c, slot);
         if (valid) {
             const longlong2* col = reinterpret_cast<const longlong2*>(cold);
-            const uint64_t ks = c << L.ell, ke = ks + (1ull << L.ell);
+            const uint64_t ks = c << L.ell;
+            // the walk counts k modulo 2^(ell+1) in 32 bits: bit ell of k is
+            // bit 0 of the chunk index, and the steps read bits 0..ell only
+            const uint32_t kb = (uint32_t)(c & 1) << L.ell, kz = kb + (1u << L.ell);
             int64_t Rr[RQ], Ri[RQ];
 #pragma unroll
             for (int k = 0; k < RQ; ++k) {
@@ -448,15 +460,15 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
             longlong2 nxt[RQ];                       // column of the step into k + 1
 #pragma unroll
             for (int r = 0; r < RQ; ++r) nxt[r] = make_longlong2(0, 0);
-            if (ks + 1 < ke) {
-                const int j = __ffsll((long long)(ks + 1)) - 1;
+            if (kb + 1 < kz) {
+                const int j = __ffs((int)(kb + 1)) - 1;
 #pragma unroll
                 for (int r = 0; r < RQ; ++r)
                     if (q + 4 * r < N) nxt[r] = __ldg(col + j * N + q + 4 * r);
             }
-            for (uint64_t k = ks; k < ke; ++k) {
-                if (k > ks) {
-                    const int j = __ffsll((long long)k) - 1;
+            for (uint32_t k = kb; k < kz; ++k) {
+                if (k > kb) {
+                    const int j = __ffs((int)k) - 1;
                     const int64_t neg = -(int64_t)((k >> (j + 1)) & 1);   // the column leaves S
 #pragma unroll
                     for (int r = 0; r < RQ; ++r) {
@@ -464,8 +476,8 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
                         Rr[r] += (nxt[r].x ^ neg) - neg;
                         Ri[r] += (nxt[r].y ^ neg) - neg;
                     }
-                    if (k + 1 < ke) {
-                        const int jn = __ffsll((long long)(k + 1)) - 1;
+                    if (k + 1 < kz) {
+                        const int jn = __ffs((int)(k + 1)) - 1;
 #pragma unroll
                         for (int r = 0; r < RQ; ++r)
                             if (q + 4 * r < N) nxt[r] = __ldg(col + jn * N + q + 4 * r);
@@ -527,10 +539,12 @@ __global__ void __launch_bounds__(kQuadThreads) ryser_x64c4_kernel(const FpLaunc
 
 template <int N>
 cudaError_t launch_x64r(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    if (L.ell < 0 || L.ell > 30) return cudaErrorInvalidValue;   // 32-bit step counter
     return launch_dependent(ryser_x64r_kernel<N>, (unsigned)grid, (unsigned)threads, s, L);
 }
 template <int N>
 cudaError_t launch_x64c(const FpLaunch& L, int grid, int threads, cudaStream_t s) {
+    if (L.ell < 0 || L.ell > 30) return cudaErrorInvalidValue;   // 32-bit step counter
     if constexpr (x64c_quad_ok<N>()) {
         // fewer one-lane warps than SM sub-partitions: four lanes per chunk (same bits)
         const uint64_t items = L.item_end - L.item_begin;
