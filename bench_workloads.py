@@ -565,9 +565,14 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
         perms = sum(len(v[1]) for v in part.values())
         row["batched_perms_per_s"] = perms / ms_b * 1e3
         row["batched_matrices"] = perms
-        # plain: one call per matrix, 8 of every (ensemble, n)
+        # plain: one call per matrix, 8 of every (ensemble, n), with the library's
+        # built-in chunking for a lone matrix (shortened to fill the GPU): the tuned
+        # chunk lengths are picked for full batches and would starve a lone call
         plain_ms, plain_perms = 0.0, 0
         for cplx, (flat, ns, offs, out) in part.items():
+            field = px.FIELD_C128 if cplx else px.FIELD_F64
+            tuned = px.perm_tune_get(field, n)
+            px.perm_tune_set(field, n, 0)
             fn = px.perm_c128 if cplx else px.perm_f64
             idx = [e * sub + k for e in range(3) for k in range(8)]
             fn(flat, ns[:1], offs[:1], out[:1], stream)
@@ -580,6 +585,7 @@ def batched_object(scale: float = 1.0, tune: bool = True) -> dict:
             torch.cuda.synchronize()
             plain_ms += a.elapsed_time(b)
             plain_perms += len(idx)
+            px.perm_tune_set(field, n, tuned)
         row["plain_perms_per_s"] = plain_perms / plain_ms * 1e3
         row["plain_matrices"] = plain_perms
         row["batched_over_plain"] = row["batched_perms_per_s"] / row["plain_perms_per_s"]
