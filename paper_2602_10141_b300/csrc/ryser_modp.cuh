@@ -246,11 +246,15 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
             // products are formed from independent arrays, which doubles the
             // instruction-level parallelism of the product trees.  r2 is
             // computed from r and the next r from r2, so no array is copied.
-            // A pair's two products enter D one pair later, so no instruction
+            // A pair's two products are summed one pair later, so no instruction
             // of the pair waits for the trees' last levels and the next pair's
             // column steps and trees issue behind them.  The loop tests once
             // per pair: the step after the last pair is taken too and unused.
+            // The pairs' even and odd products are summed apart, each offset
+            // by p into [0, 2p) (unsigned: no sign extension); every pair adds
+            // one of each, so the offsets cancel in Eu - Ou (< 2^(ell+31)).
             mont_t pe = 0, po = 0;
+            unsigned long long Eu = 0, Ou = 0;
             const uint32_t kp = ke32 - ((ke32 - k) & 1);   // pairs cover [k, kp)
             if (N <= PERMX_MODP_PAIR_MAX_N && k < kp) {
                 do {
@@ -259,7 +263,8 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                     else column_step<N, false>(r2, r, col, p, z0);
                     mont_t te, to;
                     prod_tree2<N>(r, r2, p, pinv, (int32_t)z0, te, to);
-                    D += (long long)pe - po;
+                    Eu += ((uint32_t)pe + p);
+                    Ou += ((uint32_t)po + p);
                     pe = te;
                     po = to;
                     k += 2;
@@ -270,7 +275,9 @@ __global__ void __launch_bounds__(kRyserThreads, PERMX_MODP_MINB) ryser_modp_ker
                     else column_step<N, false>(r, r2, col + j * NP, p, z0);
                 } while (k < kp);
             }
-            D += (long long)pe - po;
+            Eu += ((uint32_t)pe + p);
+            Ou += ((uint32_t)po + p);
+            D += (long long)(Eu - Ou);
             for (; k < ke32; ++k) {            // remaining steps one at a time
                 const long long t = prod_tree<N>(r, p, pinv, (int32_t)z0);
                 D += (k & 1) ? -t : t;
