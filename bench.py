@@ -46,7 +46,7 @@ WORKLOAD = "schur_n33_fp_5primes"
 # one ncu capture of the current build; not scaled to the bench launch (5 x 2^32 steps): the
 # walk reads its residue tables once and otherwise only instruction fetch reaches DRAM, which
 # does not grow in proportion to the launch
-WALK_DRAM_BYTES_SMALL_CASE = 246_528
+WALK_DRAM_BYTES_SMALL_CASE = 37_632
 
 
 def _rank_env():
