@@ -61,6 +61,8 @@ def check_plan(px, field, sizes, pinned=()):
         n = g["n"]
         # the Nijenhuis-Wilf walk: 2^(n-1) Gray steps per matrix, split into chunks
         assert g["ell"] >= 0 and g["log2_chunks"] >= 0 and g["ell"] + g["log2_chunks"] == n - 1
+        # the walks count a chunk's steps modulo 2^(ell+1) in 32 bits
+        assert g["ell"] <= 30
         assert g["items"] == g["nmats"] << g["log2_chunks"]
         # staged layout: n + 1 columns (the x column last) of ld entries
         ld = pad(n, 4) if modp else (pad(n, 2) if field == px.FIELD_F64 else n)
@@ -151,3 +153,19 @@ def test_describe_rejects_bad_arguments(px):
     n[1] = 33
     assert px._lib.permx_plan_describe(px.FIELD_F64, *args) == px.PERMX_EINVAL
     assert px._lib.permx_plan_describe(7, *args) == px.PERMX_EINVAL
+
+
+def test_longest_chunks_fit_the_step_counter(px):
+    """The longest chunk any plan may hold is 2^30 steps (the walks keep the Gray
+    index modulo 2^(ell+1) in 32 bits): a pinned F_p length of 30 is kept, and
+    the tuning table refuses anything longer."""
+    try:
+        px.perm_tune_set(px.FIELD_MODP, 48, 30)
+        g = check_plan(px, px.FIELD_MODP, [48], pinned={48})[0]
+        assert g["ell"] == 30 and g["log2_chunks"] == 17
+        with pytest.raises(px.PermxError):
+            px.perm_tune_set(px.FIELD_MODP, 48, 31)
+    finally:
+        px.perm_tune_set(px.FIELD_MODP, 48, 0)
+    for n in range(1, 49):
+        assert check_plan(px, px.FIELD_MODP, [n])[0]["ell"] <= 30
