@@ -235,8 +235,9 @@ int perm_graph_destroy(perm_graph* graph);
  * F_p batches shorten their chunks (see perm_modp).  perm_tune_set
  * pins ell for (field, n) (0 restores the built-in rule; ell <=
  * PERMX_MAX_ELL_MODP for F_p, whose chunk sums of terms below 2^31 are kept
- * in 64 bits, ell <= PERMX_MAX_ELL_FP for the float fields, whose exact
- * 128-bit chunk accumulator needs the headroom; EINVAL otherwise); perm_tune_get
+ * in 64 bits and whose walk counts a chunk's steps in 32 bits, ell <=
+ * PERMX_MAX_ELL_FP for the float fields, whose exact 128-bit chunk
+ * accumulator needs the headroom; EINVAL otherwise); perm_tune_get
  * returns the ell in force; perm_autotune times ell0-3 .. ell0+3 around the
  * built-in rule on a synthetic batch of `batch` n x n matrices (`reps`
  * passes each, each timed on its own; a candidate counts by its fastest pass),

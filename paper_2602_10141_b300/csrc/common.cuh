@@ -39,7 +39,9 @@ int cuda_fail(cudaError_t e, const char* what);
 // staged matrix then carries x as an extra column (index n).
 // ---------------------------------------------------------------------------
 int chunk_log2_modp(int bits);
-constexpr int kModpMaxEll = 30;   // longest F_p chunk (log2 steps): the walk counts k mod 2^(ell+1) in 32 bits
+// longest F_p chunk (log2 steps): the walk counts k mod 2^(ell+1) in 32 bits
+constexpr int kModpMaxEll = PERMX_MAX_ELL_MODP;
+static_assert(kModpMaxEll <= 30, "32-bit step counter");
 int chunk_log2_fp(int bits);
 inline int walk_bits(int n, int nw) { return nw ? n - 1 : n; }
 
